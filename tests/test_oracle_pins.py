@@ -1,0 +1,388 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each test checks the oracle against a closed form, an exact rational brute
+force, a conservation law, or a structural property that the mathematics or
+the paper fixes, chosen so that a dropped term, a wrong sign, a wrong index or
+a swapped operand in the oracle fails at least one of them.
+"""
+from __future__ import annotations
+
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_2203_10477_gb300 import inputs
+from tests import rational_ref as rr
+
+CAN, INC = 0, 1
+
+
+def bump(T, width=40):
+    """A smooth boundary pulse that is exactly 0 at t = 0 (and after `width`)."""
+    n = np.arange(T + 1)
+    f = np.where(n < width, np.sin(np.pi * n / width) ** 2, 0.0)
+    f[0] = 0.0
+    return f
+
+
+def dalembert_cfl1(nx, T, fA):
+    """Leapfrog at Courant number 1 with u(1,t) = 0 reproduces d'Alembert's
+    solution with image reflections exactly on the grid (M = nx - 1):
+        u_j^n = sum_{m>=0} [F(n - 2mM - j) - F(n - 2(m+1)M + j)],
+    F(s) = fA[s] for s >= 0 and 0 for s < 0 (fA[0] must be 0)."""
+    M = nx - 1
+
+    def F(s):
+        return fA[s] if s >= 0 else 0.0
+
+    u = np.zeros(nx)
+    for j in range(nx):
+        tot = 0.0
+        m = 0
+        while n_ok(T, m, M):
+            tot += F(T - 2 * m * M - j) - F(T - 2 * (m + 1) * M + j)
+            m += 1
+        u[j] = tot
+    return u
+
+
+def n_ok(T, m, M):
+    return T - 2 * m * M + M >= 0
+
+
+# ----------------------------------------------------------------------------
+# closed forms
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("form", [CAN, INC])
+def test_cfl1_equals_dalembert_with_reflections(oracle_mod, form):
+    nx, T = 101, 450  # four reflections off x = 1 and x = 0
+    dt = 1.0 / (nx - 1)  # a = 1, c = 1 exactly
+    fA = bump(T)
+    assert fA[0] == 0.0
+    out = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, np.zeros(T + 1), form=form)
+    assert out["coeffs"].c == 1.0
+    ref = dalembert_cfl1(nx, T, fA)
+    assert np.abs(ref).max() > 0.5
+    np.testing.assert_allclose(out["u"], ref, rtol=0, atol=1e-13)
+    # the previous level as well (canonical form stores it)
+    if form == CAN:
+        np.testing.assert_allclose(out["w"], dalembert_cfl1(nx, T - 1, fA), rtol=0, atol=1e-13)
+
+
+def test_cfl1_receiver_trace_is_delayed_boundary(oracle_mod):
+    """Before the first reflection the trace at j is fA delayed by j steps."""
+    nx, T, j = 401, 300, 37
+    dt = 1.0 / (nx - 1)
+    fA = bump(T, 60)
+    out = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, np.zeros(T + 1), rec_j=[j])
+    expect = np.concatenate([np.zeros(j), fA[: T + 1 - j]])
+    np.testing.assert_allclose(out["rec"][0], expect, rtol=0, atol=1e-14)
+
+
+def exact_continuous(x, t, f, L=1.0, a=1.0, terms=8):
+    """d'Alembert with images for u(0,t) = f(t), u(L,t) = 0, zero initial data."""
+    tot = np.zeros_like(x)
+    for m in range(terms):
+        tot += f(t - (x + 2 * m * L) / a) - f(t - (2 * (m + 1) * L - x) / a)
+    return tot
+
+
+def test_second_order_convergence_at_cfl_half(oracle_mod):
+    def f(t):
+        t = np.asarray(t, dtype=float)
+        # a Gaussian pulse centred 6 sigma after t = 0 (f(0) ~ 2e-16: smooth start)
+        return np.where(t > 0, np.exp(-(((t - 0.3) / 0.05) ** 2)), 0.0)
+
+    t_end = 0.7
+    errs = []
+    for nx in (101, 201, 401, 801):
+        dx = 1.0 / (nx - 1)
+        dt = 0.5 * dx
+        T = int(round(t_end / dt))
+        fA = f(np.arange(T + 1) * dt)
+        out = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, np.zeros(T + 1))
+        x = np.linspace(0, 1, nx)
+        errs.append(np.abs(out["u"] - exact_continuous(x, T * dt, f)).max())
+    ratios = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert all(3.6 < r < 4.4 for r in ratios[1:]), (errs, ratios)
+
+
+# ----------------------------------------------------------------------------
+# exact rational brute force
+# ----------------------------------------------------------------------------
+
+def _tiny_case(seed, nx=23, T=37):
+    r = inputs.rng(seed)
+    fA = np.round(r.standard_normal(T + 1) * 8) / 8  # dyadic samples: exact in binary
+    fB = np.round(r.standard_normal(T + 1) * 8) / 8
+    return nx, T, fA, fB
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+@pytest.mark.parametrize("form", [CAN, INC])
+def test_oracle_within_rounding_of_exact_rationals(oracle_mod, seed, form):
+    nx, T, fA, fB = _tiny_case(seed)
+    dt = 0.6 / (nx - 1)
+    cf = oracle_mod.coeffs(0.0, 1.0, 1.0, nx, dt)
+    c2 = Fraction(cf.c2)
+    k = Fraction(cf.k) if form == CAN else 2 - 2 * c2
+    levels = rr.leapfrog(nx, T, c2, k, fA, fB)
+    exact = np.array([float(v) for v in levels[-1]])
+    out = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, fB, form=form)
+    scale = max(1.0, np.abs(exact).max())
+    assert np.abs(out["u"] - exact).max() <= 1e-12 * scale
+    # second state component
+    if form == CAN:
+        prev = np.array([float(v) for v in levels[-2]])
+        assert np.abs(out["w"] - prev).max() <= 1e-12 * scale
+    else:
+        v = np.array([float(a - b) for a, b in zip(levels[-1], levels[-2])])
+        assert np.abs(out["w"] - v).max() <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("N,ov", [(2, 4), (3, 6), (4, 5), (3, 8)])
+def test_rswr_mask_exact_in_rationals_and_tight(N, ov):
+    """Decomposition + Prediction Validation + Global Span theorems (Sec. 2.2,
+    2.4, 3) on the discrete scheme: with S <= floor(ov/2) the combined RSWR
+    state equals the monolithic state exactly; S = floor(ov/2) + 1 does not."""
+    nx, T, fA, fB = _tiny_case(7 + N + ov, nx=31, T=29)
+    c2 = Fraction(9, 25)
+    k = 2 - 2 * c2
+    mono = rr.leapfrog(nx, T, c2, k, fA, fB)
+    S = ov // 2
+    u, prev = rr.rswr_mask(nx, T, c2, k, fA, fB, N, ov, S)
+    assert u == mono[-1] and prev == mono[-2]
+    u_bad, _ = rr.rswr_mask(nx, T, c2, k, fA, fB, N, ov, S + 1)
+    assert u_bad != mono[-1]
+
+
+def test_tangent_linear_matches_oracle_adjoint_dc2(oracle_mod):
+    """d/dc2 of a linear functional of the receiver trace: exact forward-mode
+    differentiation in rationals vs the oracle's discrete adjoint."""
+    nx, T, fA, fB = _tiny_case(11, nx=19, T=33)
+    fB = np.zeros(T + 1)
+    dt = 0.7 / (nx - 1)
+    cf = oracle_mod.coeffs(0.0, 1.0, 1.0, nx, dt)
+    r = inputs.rng(12)
+    wbar = np.round(r.standard_normal(T + 1) * 4) / 4
+    jr = 9
+    exact = rr.tangent_dc2(nx, T, Fraction(cf.c2), fA, fB, jr, [Fraction(x) for x in wbar])
+    g = oracle_mod.adjoint(nx, T, 1.0, dt, fA, fB, jr, wbar)
+    assert abs(g["dc2"] - float(exact)) <= 1e-11 * max(1.0, g["abs_dc2"])
+
+
+# ----------------------------------------------------------------------------
+# structural properties
+# ----------------------------------------------------------------------------
+
+def test_discrete_energy_is_conserved(oracle_mod):
+    """With u = 0 on both ends the leapfrog conserves
+    E^{n+1/2} = ||u^{n+1} - u^n||^2 + c^2 <D u^{n+1}, D u^n>  (D = forward difference)."""
+    nx = 257
+    dt = 0.8 / (nx - 1)
+    u0 = inputs.smooth_random_state(nx, seed=3)
+    z = lambda T: np.zeros(T + 1)
+
+    def energy(T):
+        out = oracle_mod.leapfrog(nx, T, 1.0, dt, z(T), z(T), q0=u0, q1=u0)
+        un, up = out["u"], out["w"]
+        c2 = out["coeffs"].c2
+        return np.sum((un - up) ** 2) + c2 * np.sum(np.diff(un) * np.diff(up))
+
+    E = [energy(T) for T in (1, 17, 400, 1300)]
+    assert E[0] > 1e-3
+    np.testing.assert_allclose(E, E[0], rtol=1e-12)
+
+
+def test_light_cone_and_causal_truncation(oracle_mod):
+    """Zero initial data, quiet right end: u_j^n = 0 exactly for j > n, so a
+    grid truncated to T + 2 points reproduces the full grid bit for bit."""
+    nx, T = 3000, 700
+    dt = 0.9 / (nx - 1)
+    fA = inputs.gaussian_pulse(T, dt, sigma_steps=20)
+    full = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, np.zeros(T + 1), rec_j=[350])
+    assert np.all(full["u"][T + 1:] == 0.0)
+    assert full["u"][T] != 0.0
+    n_run = oracle_mod.causal_extent(T, nx)
+    cut = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, np.zeros(T + 1), rec_j=[350], nx_run=n_run)
+    assert np.array_equal(cut["u"], full["u"][:n_run])
+    assert np.array_equal(cut["w"], full["w"][:n_run])
+    assert np.array_equal(cut["rec"], full["rec"])
+
+
+def test_forms_agree_in_fp64(oracle_mod):
+    p = inputs.c1()
+    a = oracle_mod.leapfrog(p.nx, p.T, p.a, p.dt, p.fA, p.fB, form=CAN)
+    b = oracle_mod.leapfrog(p.nx, p.T, p.a, p.dt, p.fA, p.fB, form=INC)
+    assert np.abs(a["u"] - b["u"]).max() <= 1e-12 * np.abs(a["u"]).max()
+    assert np.abs(a["u"] - b["u"]).max() > 0  # they are different operation orders
+
+
+def test_fp32_increment_form_within_1e5_of_fp64(oracle_mod):
+    nx, T = 6000, 5000
+    dt = 0.9 / (nx - 1)
+    fA = inputs.gaussian_pulse(T, dt)
+    ref = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, np.zeros(T + 1))
+    f32 = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, np.zeros(T + 1), form=INC, prec="f32")
+    err = np.abs(f32["u"].astype(np.float64) - ref["u"]).max() / np.abs(ref["u"]).max()
+    assert err <= 1e-5, err
+
+
+def test_t0_returns_initial_state(oracle_mod):
+    nx = 40
+    u0 = inputs.smooth_random_state(nx, seed=5)
+    f = np.array([0.25])
+    out = oracle_mod.leapfrog(nx, 0, 1.0, 0.5 / (nx - 1), f, f * 0, q0=u0)
+    expect = u0.copy()
+    expect[0], expect[-1] = 0.25, 0.0
+    assert np.array_equal(out["u"], expect)
+    assert np.array_equal(out["w"], expect)  # canonical: at rest, u^{-1} = u^0
+
+
+# ----------------------------------------------------------------------------
+# RSWR invariants on the oracle
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("form", [CAN, INC])
+@pytest.mark.parametrize("nx,N,ov,T,S", [
+    (1001, 2, 16, 300, None),
+    (1001, 2, 16, 300, 5),
+    (997, 7, 10, 211, None),
+    (640, 10, 15, 173, None),
+    (515, 1, 8, 97, None),
+])
+def test_rswr_mask_equals_monolithic_bitwise(oracle_mod, prec, form, nx, N, ov, T, S):
+    dt = 0.7 / (nx - 1)
+    fA = inputs.ramped_sine(T, dt, freq=20.0)
+    fB = 0.3 * inputs.ramped_sine(T, dt, freq=11.0)
+    q0 = inputs.smooth_random_state(nx, seed=nx)
+    mono = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, fB, form=form, prec=prec, q0=q0)
+    rs = oracle_mod.rswr_mask(nx, T, 1.0, dt, fA, fB, N, ov, S=S, form=form, prec=prec, q0=q0)
+    assert np.array_equal(rs["u"], mono["u"])
+    assert np.array_equal(rs["w"], mono["w"])
+
+
+def test_rswr_mask_too_long_span_differs(oracle_mod):
+    nx, N, ov, T = 1001, 4, 16, 300
+    dt = 0.7 / (nx - 1)
+    q0 = inputs.smooth_random_state(nx, seed=9)
+    z = np.zeros(T + 1)
+    mono = oracle_mod.leapfrog(nx, T, 1.0, dt, z, z, q0=q0)
+    bad = oracle_mod.rswr_mask(nx, T, 1.0, dt, z, z, N, ov, S=ov // 2 + 1, q0=q0)
+    assert not np.array_equal(bad["u"], mono["u"])
+
+
+def test_rswr_output_waveforms_equal_true_fluxes(oracle_mod):
+    """Prediction Validation Theorem (Sec. 2.4): within the span the predicted
+    boundary output waveforms are the true ones."""
+    nx, N, ov, T = 801, 5, 12, 260
+    dt = 0.8 / (nx - 1)
+    q0 = inputs.smooth_random_state(nx, seed=4)
+    fA = inputs.ramped_sine(T, dt, freq=9.0)
+    z = np.zeros(T + 1)
+    rs = oracle_mod.rswr_mask(nx, T, 1.0, dt, fA, z, N, ov, q0=q0)
+    el, er = (ov + 1) // 2, ov // 2
+    pts = []
+    for i in range(N - 1):
+        b1 = (i + 1) * nx // N
+        pts += [b1 - el, b1 - 1 + er]
+    mono = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, z, q0=q0, flux_j=pts)
+    assert np.array_equal(rs["traces"].reshape(-1, T + 1), mono["flux"])
+    assert np.abs(mono["flux"]).max() > 1.0
+
+
+@pytest.mark.parametrize("N,ov,cfl", [(2, 16, 0.5), (10, 16, 0.5), (4, 24, 0.9), (3, 9, 0.7)])
+def test_rswr_paper_literal_matches_monolithic(oracle_mod, N, ov, cfl):
+    nx, T = 1001, 600
+    dt = cfl / (nx - 1)
+    fA = inputs.ramped_sine(T, dt, freq=7.0)
+    z = np.zeros(T + 1)
+    mono = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, z)
+    pl = oracle_mod.rswr_paper(nx, T, 1.0, dt, fA, z, N, ov)
+    scale = np.abs(mono["u"]).max()
+    assert np.abs(pl["u"] - mono["u"]).max() <= 1e-12 * scale
+    cap = math.ceil((ov - 1) / (2 * pl["coeffs"].c)) - 1
+    assert pl["spans"].sum() == T
+    assert pl["spans"].max() <= cap and pl["spans"].min() >= 1
+
+
+# ----------------------------------------------------------------------------
+# adjoint
+# ----------------------------------------------------------------------------
+
+def _adj_case(nx=301, T=420, jr=120):
+    dt = 0.9 / (nx - 1) / 1.3  # Courant number 0.9 at a = 1.3
+    g = inputs.lowpass_noise(T, seed=21)
+    return nx, T, dt, g, jr
+
+
+def test_adjoint_dot_product(oracle_mod):
+    nx, T, dt, g, jr = _adj_case()
+    z = np.zeros(T + 1)
+    r = inputs.rng(3)
+    dgv = r.standard_normal(T + 1)
+    w = r.standard_normal(T + 1)
+    Jdg = oracle_mod.leapfrog(nx, T, 1.3, dt, dgv, z, rec_j=[jr])["rec"][0]
+    JTw = oracle_mod.adjoint(nx, T, 1.3, dt, g, z, jr, w)["dg"]
+    lhs, rhs = np.dot(Jdg, w), np.dot(dgv, JTw)
+    assert abs(lhs - rhs) <= 1e-13 * max(abs(lhs), np.abs(Jdg * w).sum())
+
+
+def test_adjoint_gradient_g_matches_central_difference(oracle_mod):
+    nx, T, dt, g, jr = _adj_case()
+    z = np.zeros(T + 1)
+    target = oracle_mod.leapfrog(nx, T, 1.0, dt, g, z, rec_j=[jr])["rec"][0]
+    res = oracle_mod.misfit_grad(nx, T, 1.3, dt, g, z, jr, target)
+    d = inputs.rng(8).standard_normal(T + 1)
+    for h in (1e-2, 1.0):  # the loss is quadratic in g: exact for any h
+        lp = oracle_mod.misfit_grad(nx, T, 1.3, dt, g + h * d, z, jr, target)["loss"]
+        lm = oracle_mod.misfit_grad(nx, T, 1.3, dt, g - h * d, z, jr, target)["loss"]
+        fd = (lp - lm) / (2 * h)
+        an = np.dot(res["dg"], d)
+        assert abs(fd - an) <= 1e-8 * abs(an), (h, fd, an)
+
+
+def test_adjoint_gradient_a_matches_central_difference(oracle_mod):
+    """Central differences in a converge to the adjoint dL/da at O(h^2)."""
+    nx, T, dt, g, jr = _adj_case()
+    z = np.zeros(T + 1)
+    target = oracle_mod.leapfrog(nx, T, 1.0, dt, g, z, rec_j=[jr])["rec"][0]
+    a = 1.3
+    res = oracle_mod.misfit_grad(nx, T, a, dt, g, z, jr, target)
+    errs = []
+    for rel in (1e-4, 1e-5, 1e-6):
+        h = rel * a
+        lp = oracle_mod.misfit_grad(nx, T, a + h, dt, g, z, jr, target)["loss"]
+        lm = oracle_mod.misfit_grad(nx, T, a - h, dt, g, z, jr, target)["loss"]
+        errs.append(abs((lp - lm) / (2 * h) - res["da"]) / abs(res["da"]))
+    assert 80 < errs[0] / errs[1] < 120, errs  # second order in h
+    assert errs[2] < 1e-8, errs
+
+
+def test_adjoint_boundary_receiver_and_unreachable_receiver(oracle_mod):
+    nx, T, dt, g, _ = _adj_case(T=100)
+    z = np.zeros(T + 1)
+    w = inputs.rng(2).standard_normal(T + 1)
+    # receiver on the Dirichlet node: the trace is g itself, so dL/dg = wbar and dL/da = 0
+    res = oracle_mod.adjoint(nx, T, 1.3, dt, g, z, 0, w)
+    assert np.array_equal(res["dg"], w)
+    assert res["dc2"] == 0.0
+    # receiver beyond the reach of T steps: every gradient is exactly zero
+    res = oracle_mod.adjoint(nx, T, 1.3, dt, g, z, T + 5, w)
+    assert np.all(res["dg"] == 0.0) and res["dc2"] == 0.0
+
+
+def test_adjoint_causal_truncation_is_exact(oracle_mod):
+    nx, T, jr = 5000, 300, 140
+    dt = 0.9 / (nx - 1) / 1.3
+    g = inputs.lowpass_noise(T, seed=4)
+    z = np.zeros(T + 1)
+    w = inputs.rng(5).standard_normal(T + 1)
+    full = oracle_mod.adjoint(nx, T, 1.3, dt, g, z, jr, w)
+    cut = oracle_mod.adjoint(nx, T, 1.3, dt, g, z, jr, w, nx_run=oracle_mod.causal_extent(T, nx))
+    assert np.array_equal(full["dg"], cut["dg"])
+    assert full["dc2"] == cut["dc2"]
