@@ -1,0 +1,263 @@
+/*
+ * rswr.h -- C ABI of librswr: Relative Schwarz Waveform Relaxation (RSWR) for
+ * the 1-D wave equation on NVIDIA GB300 (sm_103a).
+ *
+ * Method: F. Wei and A. Zhao, "A Non-iterative Overlapping Schwarz Waveform
+ * Relaxation Algorithm for Wave Equation", arXiv 2203.10477.
+ *
+ * Problem (paper Sec. 2.1, Eq. (2.1)-(2.3)):
+ *     u_tt = a^2 u_xx on [xa, xb], a > 0,
+ *     u(x, 0) = 0, u_t(x, 0) = 0   (or a caller-supplied state),
+ *     u(xa, t) = f_A(t),  u(xb, t) = f_B(t).
+ * Discretisation (the paper fixes none): grid x_j = xa + j dx, j = 0..nx-1,
+ * dx = (xb - xa)/(nx - 1); level n is t = n dt; second-order central leapfrog
+ * with Courant number c = a dt / dx <= 1, c2 = c*c, k = 2 - 2 c2:
+ *     canonical form:  u^{n+1}_j = fma(c2, u^n_{j-1} + u^n_{j+1}, fma(k, u^n_j, -u^{n-1}_j))
+ *     increment form:  v^{n+1}_j = fma(c2, (u^n_{j+1} - u^n_j) - (u^n_j - u^n_{j-1}), v^n_j),
+ *                      u^{n+1}_j = u^n_j + v^{n+1}_j            (v^n = u^n - u^{n-1})
+ * Both are evaluated in exactly this operation order with correctly rounded
+ * IEEE arithmetic, so results are reproducible bit for bit.  Coefficients are
+ * computed once in double (c = a*dt/dx, c2 = c*c, k = 2 - 2*c2,
+ * inv2dx = 1/(2 dx)); an F32 plan rounds c2 and inv2dx to float and computes
+ * k = 2 - 2*c2 in float.
+ *
+ * A state is a pair of arrays (q0, q1) of nx points each:
+ *     canonical form: q0 = u^n, q1 = u^{n-1};   increment form: q0 = u^n, q1 = v^n.
+ * At level 0 the boundary entries are always overwritten with the Dirichlet
+ * samples (q0) and "at rest" values (q1 = q0 canonical, q1 = 0 increment).
+ *
+ * Decomposition (paper Sec. 2.2, Sec. 3): n_sub overlapping subdomains in a
+ * row.  Core i is [b_i, b_{i+1} - 1] with b_i = floor(i * nx / n_sub); its
+ * window extends ceil(ov/2) points to the left and floor(ov/2) points to the
+ * right (clipped to the grid), so neighbours share exactly `overlap` points.
+ * One time span is S steps with S <= floor(overlap/2): the discrete form of the
+ * Waveform Time Span Theorem (Sec. 2.4) for a scheme whose domain of dependence
+ * grows one point per step.  Each span runs predict (Sec. 2.3, zero input flux
+ * guess), select (Sec. 2.4, index mask) and update (Sec. 2.5, core write-back),
+ * and the loop restarts from the combined state (Sec. 2.6).  The combined state
+ * equals the monolithic leapfrog bit for bit.
+ *
+ * Conventions
+ *   - All data pointers are DEVICE pointers owned by the caller unless a
+ *     function says otherwise; the library never frees them.
+ *   - Element type of every data array is float for RSWR_F32 plans and double
+ *     for RSWR_F64 plans.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on that stream; host arguments are
+ *     consumed before the call returns.
+ *   - A plan or batch may be used by one stream at a time; it is not
+ *     thread-safe.
+ *   - No exception crosses the ABI.  Every call returns an rswr_status; the
+ *     detail of the last failure on the calling thread is in
+ *     rswr_last_error_message().  Device-side failures (a bounded wait that
+ *     expired) are latched on the device and reported by rswr_plan_check /
+ *     rswr_batch_check.
+ */
+#ifndef RSWR_H
+#define RSWR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rswr_status {
+    RSWR_OK = 0,
+    RSWR_EINVAL = 1,     /* bad argument: NULL where required, size out of range, T < 0 */
+    RSWR_ECFL = 2,       /* Courant number a*dt/dx > 1: the leapfrog would be unstable */
+    RSWR_EOVERLAP = 3,   /* overlap < 2, a core shorter than the overlap, or S > floor(ov/2) */
+    RSWR_ENOMEM = 4,     /* device or host allocation failed */
+    RSWR_ECUDA = 5,      /* a CUDA runtime call failed (message has the CUDA error) */
+    RSWR_ETIMEOUT = 6,   /* a bounded device-side wait expired (kernel returned early) */
+    RSWR_ENOTSUP = 7     /* unsupported dtype / form / device */
+} rswr_status;
+
+typedef enum rswr_dtype { RSWR_F32 = 0, RSWR_F64 = 1 } rswr_dtype;
+
+/* RSWR_FORM_DEFAULT = canonical for F64, increment for F32 (the canonical form
+ * accumulates too much rounding in float over 10^4 steps). */
+typedef enum rswr_form { RSWR_FORM_DEFAULT = 0, RSWR_FORM_CANONICAL = 1, RSWR_FORM_INCREMENT = 2 } rswr_form;
+
+/* How the spans of a run are scheduled on the GPU. */
+typedef enum rswr_mode {
+    RSWR_MODE_PERSISTENT = 0, /* one launch for all spans; per-tile neighbour flags (default) */
+    RSWR_MODE_PER_SPAN = 1    /* one launch per span (the span loop of Sec. 2.6 on the host) */
+} rswr_mode;
+
+const char* rswr_status_string(rswr_status s);
+const char* rswr_last_error_message(void);
+int32_t rswr_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Plans: one problem                                                        */
+/* ------------------------------------------------------------------------ */
+
+typedef struct rswr_plan_s* rswr_plan_t;
+
+/* Creates a plan for one problem (paper Sec. 2.1 problem, Sec. 2.2 / Sec. 3
+ * decomposition into n_sub subdomains sharing `overlap` points).
+ * Allocates the plan's device workspace (two ping-pong state pairs of the
+ * padded grid) on the current device.  flags: reserved, pass 0.
+ * Errors: EINVAL (nx < 3, n_sub < 1, a <= 0, dt <= 0, xb <= xa, bad dtype or
+ * form), ECFL, EOVERLAP (overlap < 2 or floor(nx/n_sub) < overlap), ENOMEM,
+ * ECUDA.  On error *plan is NULL. */
+rswr_status rswr_plan_create(rswr_plan_t* plan, double xa, double xb, double a, int64_t nx, double dt,
+                             int32_t n_sub, int32_t overlap, int32_t dtype, int32_t form, uint32_t flags);
+
+/* Frees the plan and its workspace (synchronises the device first). NULL is a no-op. */
+void rswr_plan_destroy(rswr_plan_t plan);
+
+typedef struct rswr_plan_info {
+    int64_t nx;
+    int32_t dtype, form, n_sub, overlap;
+    double c, c2, k, inv2dx;         /* double coefficients */
+    float c2f, kf, inv2dxf;          /* F32 coefficients */
+    int32_t span_steps;              /* S */
+    int32_t halo;                    /* H >= S: halo of a CTA window */
+    int32_t core;                    /* owned points per CTA tile */
+    int32_t window;                  /* points per CTA window = core + 2H */
+    int32_t points_per_thread, threads_per_cta, variant, mode;
+    int64_t ntiles;                  /* CTA tiles covering the grid */
+    int64_t state_len;               /* elements of one padded state array */
+    int64_t workspace_bytes;
+} rswr_plan_info;
+
+rswr_status rswr_plan_get_info(rswr_plan_t plan, rswr_plan_info* info);
+
+/* Steps per span, 1 <= S <= floor(overlap/2) (else EOVERLAP). */
+rswr_status rswr_plan_set_span(rswr_plan_t plan, int32_t S);
+
+/* Kernel variant (points per thread x threads per CTA) for the plan's dtype
+ * and form; see rswr_variant_count / rswr_variant_get.  Re-tiles the grid. */
+rswr_status rswr_plan_set_variant(rswr_plan_t plan, int32_t variant);
+rswr_status rswr_plan_set_mode(rswr_plan_t plan, int32_t mode);
+
+/* Upper bound, in seconds, of every device-side wait (default 5 s). */
+rswr_status rswr_plan_set_wait_limit(rswr_plan_t plan, double seconds);
+
+/* Failure-injection hook for tests: in persistent mode, CTA tile `tile` does
+ * not publish completion of span `span`, so its neighbours' bounded waits
+ * expire and the run reports RSWR_ETIMEOUT.  tile = -1 disables. */
+rswr_status rswr_plan_inject_missing_flag(rswr_plan_t plan, int32_t tile, int32_t span);
+
+/* Times every kernel variant of the plan's dtype/form (and both modes) on
+ * `probe_steps` steps of a zero-data run and keeps the fastest; returns its
+ * index in *variant (may be NULL).  Uses the plan's workspace; synchronous. */
+rswr_status rswr_plan_autotune(rswr_plan_t plan, int64_t probe_steps, int32_t* variant, void* stream);
+
+/* Waits for `stream`, then reports a device-side failure latched by the last
+ * run (RSWR_ETIMEOUT) or RSWR_OK.  code/tile/span may be NULL. */
+rswr_status rswr_plan_check(rswr_plan_t plan, void* stream, int32_t* code, int32_t* tile, int32_t* span);
+
+/*
+ * THE HOT PATH.  Advances the problem T steps (t_end = T dt) by RSWR spans.
+ *   fA, fB   Dirichlet samples f_A(n dt), f_B(n dt), n = 0..T (T+1 values);
+ *            NULL means identically 0.
+ *   q0, q1   initial state pair (nx each) or NULL: q0 = NULL gives zero data
+ *            (paper Sec. 2.1); q1 = NULL with q0 given starts at rest.
+ *   out0,out1  final state pair (nx each); required.
+ *   traces   NULL, or (n_sub-1) x 2 x (T+1) values: the boundary output
+ *            waveforms (paper Sec. 2.2 definitions) of every interface i
+ *            between subdomains i and i+1 at every level:
+ *              traces[(2i+0)(T+1)+n] = flux of subdomain i at the left end of subdomain i+1,
+ *              traces[(2i+1)(T+1)+n] = flux of subdomain i+1 at the right end of subdomain i,
+ *            flux = (u_{j+1} - u_{j-1}) * inv2dx.
+ *   j_r, recv  receiver: recv[n] = u^n_{j_r}, n = 0..T (recv may be NULL; j_r
+ *            ignored then).
+ * Errors: EINVAL, ECUDA.  Device-side timeouts: see rswr_plan_check.
+ */
+rswr_status rswr_run(rswr_plan_t plan, const void* fA, const void* fB, int64_t T, const void* q0, const void* q1,
+                     void* out0, void* out1, void* traces, int64_t j_r, void* recv, void* stream);
+
+/* Same as rswr_run with every pointer a HOST pointer: the call copies the
+ * inputs to plan-owned device buffers, runs, copies the outputs back and
+ * synchronises `stream` before returning.  Page-locked host memory makes the
+ * copies asynchronous DMA. */
+rswr_status rswr_run_host(rswr_plan_t plan, const void* fA, const void* fB, int64_t T, const void* q0,
+                          const void* q1, void* out0, void* out1, void* traces, int64_t j_r, void* recv,
+                          void* stream);
+
+/* The monolithic comparator: the same arguments and results as rswr_run,
+ * computed by one whole-grid leapfrog step per launch (no decomposition, the
+ * paper's true solution of Sec. 2.1).  Bit-identical to rswr_run. */
+rswr_status rswr_mono(rswr_plan_t plan, const void* fA, const void* fB, int64_t T, const void* q0, const void* q1,
+                      void* out0, void* out1, void* traces, int64_t j_r, void* recv, void* stream);
+
+/*
+ * Discrete adjoint (not in the paper; the gradient workload of this library).
+ * For the receiver trace y^n = u^n_{j_r} of a zero-data run with Dirichlet
+ * samples fA, fB, and a cotangent wbar = dL/dy (T+1 values), computes
+ *   grad_fA[n] = dL/dfA[n]   (T+1 values, required),
+ *   grad_a[0]  = dL/da       (one double, device pointer; NULL skips it).
+ * The adjoint variables obey the leapfrog backward in time with zero
+ * Dirichlet data and the source wbar at j_r; they run through the same span
+ * kernel.  dL/da pairs them with the forward levels, recomputed from
+ * span-boundary checkpoints (sqrt(#spans) of them) inside shared memory.
+ * Canonical plans give grad_fA bit-identical to a plain FP64 discrete adjoint
+ * of the canonical leapfrog.
+ */
+rswr_status rswr_adjoint(rswr_plan_t plan, const void* fA, const void* fB, int64_t T, int64_t j_r,
+                         const void* wbar, void* grad_fA, double* grad_a, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batches: many independent problems in one launch                          */
+/* ------------------------------------------------------------------------ */
+
+typedef struct rswr_problem {
+    int64_t nx;
+    double xa, xb, a, dt;
+    int32_t n_sub, overlap;
+} rswr_problem;
+
+typedef struct rswr_batch_s* rswr_batch_t;
+
+/* A batch of nprob independent problems with one dtype and form.  Every
+ * problem is validated like rswr_plan_create.  The span S of the batch is the
+ * smallest floor(overlap/2) over its problems (global maximum span, paper
+ * Sec. 3).  Packed arrays: problem p occupies [off[p], off[p+1]) of a packed
+ * state array (off[0] = 0, off[p+1] = off[p] + nx_p) and rows p*(T+1) ..
+ * p*(T+1)+T of a packed waveform array. */
+rswr_status rswr_batch_create(rswr_batch_t* batch, int32_t nprob, const rswr_problem* problems, int32_t dtype,
+                              int32_t form, uint32_t flags);
+void rswr_batch_destroy(rswr_batch_t batch);
+
+/* Writes the nprob+1 packed offsets (host array). */
+rswr_status rswr_batch_offsets(rswr_batch_t batch, int64_t* offsets);
+rswr_status rswr_batch_get_info(rswr_batch_t batch, rswr_plan_info* info);
+rswr_status rswr_batch_set_mode(rswr_batch_t batch, int32_t mode);
+rswr_status rswr_batch_set_variant(rswr_batch_t batch, int32_t variant);
+rswr_status rswr_batch_set_wait_limit(rswr_batch_t batch, double seconds);
+rswr_status rswr_batch_check(rswr_batch_t batch, void* stream, int32_t* code, int32_t* tile, int32_t* span);
+
+/* All problems advance T steps in one persistent launch (default mode).
+ *   fA, fB   packed waveforms nprob x (T+1), or NULL (zero)
+ *   q0, q1   packed initial states or NULL; out0, out1 packed final states (required)
+ *   j_r      HOST array of nprob receiver indices (-1 = none) or NULL
+ *   recv     packed receiver traces nprob x (T+1), or NULL */
+rswr_status rswr_batch_run(rswr_batch_t batch, const void* fA, const void* fB, int64_t T, const void* q0,
+                           const void* q1, void* out0, void* out1, const int64_t* j_r, void* recv, void* stream);
+
+/* Per-problem gradients of the receiver-trace functional (see rswr_adjoint):
+ *   j_r      HOST array of nprob receiver indices (required, 0 <= j_r < nx_p)
+ *   wbar     packed cotangents nprob x (T+1)
+ *   grad_fA  packed nprob x (T+1) outputs
+ *   grad_a   device double[nprob] or NULL */
+rswr_status rswr_batch_adjoint(rswr_batch_t batch, const void* fA, const void* fB, int64_t T, const int64_t* j_r,
+                               const void* wbar, void* grad_fA, double* grad_a, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Kernel variants                                                           */
+/* ------------------------------------------------------------------------ */
+
+int32_t rswr_variant_count(void);
+/* dtype, form (RSWR_FORM_CANONICAL / RSWR_FORM_INCREMENT), points per thread
+ * and threads per CTA of variant v. */
+rswr_status rswr_variant_get(int32_t v, int32_t* dtype, int32_t* form, int32_t* points_per_thread,
+                             int32_t* threads_per_cta);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSWR_H */

@@ -1,0 +1,1110 @@
+// rswr_api.cu -- host runtime of librswr: plans, batches, the padded state
+// layout, the probe tables, and the run / adjoint entry points of include/rswr.h.
+//
+// A plan is a batch of one problem.  Both are an Engine: a list of problems,
+// each tiled into CTA windows of W = core + 2H points, stored back to back in
+// four padded state arrays (two ping-pong pairs).  Device memory is allocated
+// once at creation and reused by every run.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/rswr.h"
+#include "rswr_internal.h"
+
+using namespace rswr;
+
+namespace {
+
+thread_local std::string g_msg;
+
+rswr_status fail(rswr_status st, const std::string& m)
+{
+    g_msg = m;
+    return st;
+}
+
+#define RSWR_CUDA(call)                                                                            \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(RSWR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));           \
+    } while (0)
+
+constexpr int kSpanCap = 256;     // largest span a CTA window supports
+constexpr int64_t kAlign = 32;    // every problem region starts on a 32-element boundary
+
+struct ProbHost {
+    int64_t nx;
+    double xa, xb, a, dt;
+    int32_t n_sub, ov;
+    double c, c2, k, inv2dx;
+    float c2f, kf, inv2dxf;
+    int64_t base = 0, tile0 = 0, ntiles = 0, off = 0;
+};
+
+// Coefficients of paper Eq. (2.1) on the uniform grid (see include/rswr.h).
+void coefficients(ProbHost& p)
+{
+    const double dx = (p.xb - p.xa) / (double)(p.nx - 1);
+    p.c = p.a * p.dt / dx;
+    p.c2 = p.c * p.c;
+    p.k = 2.0 - 2.0 * p.c2;
+    p.inv2dx = 1.0 / (2.0 * dx);
+    p.c2f = (float)p.c2;
+    p.kf = 2.0f - 2.0f * p.c2f;
+    p.inv2dxf = (float)p.inv2dx;
+}
+
+rswr_status validate(const rswr_problem& q)
+{
+    if (q.nx < 3) return fail(RSWR_EINVAL, "nx must be >= 3");
+    if (!(q.a > 0.0) || !(q.dt > 0.0) || !(q.xb > q.xa)) return fail(RSWR_EINVAL, "need a > 0, dt > 0, xb > xa");
+    if (q.n_sub < 1) return fail(RSWR_EINVAL, "n_sub must be >= 1");
+    if (q.overlap < 2) return fail(RSWR_EOVERLAP, "overlap must be >= 2");
+    if (q.nx / q.n_sub < q.overlap) return fail(RSWR_EOVERLAP, "every core must hold at least `overlap` points");
+    ProbHost p{};
+    p.nx = q.nx; p.xa = q.xa; p.xb = q.xb; p.a = q.a; p.dt = q.dt;
+    coefficients(p);
+    if (!(p.c <= 1.0)) return fail(RSWR_ECFL, "Courant number a*dt/dx = " + std::to_string(p.c) + " > 1");
+    return RSWR_OK;
+}
+
+struct Engine {
+    int dtype = kF64;
+    int form = kCanonical;
+    int device = 0;
+    int num_sms = 1;
+    int variant = 0;
+    int mode = RSWR_MODE_PERSISTENT;
+    double wait_s = 5.0;
+    int S = 1, H = 4, W = 0, core = 0, P = 0, NT = 0;
+    int inject_tile = -1, inject_span = -1;
+    bool is_plan = true;
+
+    std::vector<ProbHost> probs;
+    int64_t ntiles = 0, state_len = 0, packed_len = 0;
+    std::vector<TileDev> h_tiles;
+    std::vector<int64_t> h_offsets;
+
+    void* q0[2] = {nullptr, nullptr};
+    void* q1[2] = {nullptr, nullptr};
+    size_t state_cap = 0;  // elements allocated per state array
+    void* d_problems = nullptr;
+    void* d_tiles = nullptr;
+    size_t tiles_cap = 0;
+    void* d_probes = nullptr;
+    size_t probes_cap = 0;
+    int64_t* d_offsets = nullptr;
+    unsigned long long* d_ticket = nullptr;
+    int* d_done = nullptr;
+    size_t done_cap = 0;
+    DevError* d_err = nullptr;
+    void* d_host_stage = nullptr;  // rswr_run_host staging
+    size_t host_stage_cap = 0;
+    void* d_scratch[2] = {nullptr, nullptr};  // adjoint scratch outputs
+    size_t scratch_cap = 0;
+
+    size_t esize() const { return dtype == kF64 ? 8 : 4; }
+};
+
+void free_engine(Engine* e)
+{
+    if (!e) return;
+    cudaDeviceSynchronize();
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(e->q0[b]);
+        cudaFree(e->q1[b]);
+        cudaFree(e->d_scratch[b]);
+    }
+    cudaFree(e->d_problems);
+    cudaFree(e->d_tiles);
+    cudaFree(e->d_probes);
+    cudaFree(e->d_offsets);
+    cudaFree(e->d_ticket);
+    cudaFree(e->d_done);
+    cudaFree(e->d_err);
+    cudaFree(e->d_host_stage);
+    delete e;
+}
+
+int default_variant(int dtype, int form)
+{
+    // first registered variant of the dtype/form is the default
+    for (int v = 0; v < span_variant_count(); ++v) {
+        const VariantInfo vi = span_variant_info(v);
+        if (vi.dtype == dtype && vi.form == form) return v;
+    }
+    return -1;
+}
+
+// Lays out tiles and padded problem regions for the current variant and S;
+// (re)allocates the state arrays when they grow.
+rswr_status layout(Engine* e)
+{
+    const VariantInfo vi = span_variant_info(e->variant);
+    e->P = vi.P;
+    e->NT = vi.NT;
+    e->W = vi.P * vi.NT;
+    e->H = (e->S + 3) / 4 * 4;
+    e->core = e->W - 2 * e->H;
+    if (e->core < e->H || e->core < 4) return fail(RSWR_EINVAL, "span too long for the CTA window of this variant");
+    const int64_t pad = e->H + 8;
+    int64_t at = 0, tile = 0, off = 0;
+    e->h_tiles.clear();
+    e->h_offsets.assign(e->probs.size() + 1, 0);
+    for (size_t p = 0; p < e->probs.size(); ++p) {
+        ProbHost& ph = e->probs[p];
+        ph.ntiles = (ph.nx + e->core - 1) / e->core;
+        ph.base = at + pad;
+        ph.tile0 = tile;
+        ph.off = off;
+        for (int64_t t = 0; t < ph.ntiles; ++t) e->h_tiles.push_back(TileDev{(int32_t)p, (int32_t)t, 0, 0});
+        int64_t len = pad + ph.ntiles * e->core + pad;
+        len = (len + kAlign - 1) / kAlign * kAlign;
+        at += len;
+        tile += ph.ntiles;
+        off += ph.nx;
+        e->h_offsets[p + 1] = off;
+    }
+    e->ntiles = tile;
+    e->state_len = at;
+    // alignment contract of the 1-D bulk copies: windows and cores start on
+    // 16-byte boundaries and span whole 16-byte units
+    if (e->H % 4 || e->core % 4 || e->W % 4) return fail(RSWR_EINVAL, "internal: misaligned tiling");
+    for (const ProbHost& ph : e->probs)
+        if (ph.base % 4 || ph.base - e->H < 0) return fail(RSWR_EINVAL, "internal: misaligned problem base");
+    e->packed_len = off;
+    if (e->ntiles > (int64_t)1 << 31) return fail(RSWR_EINVAL, "too many tiles");
+
+    const size_t es = e->esize();
+    if ((size_t)e->state_len > e->state_cap) {
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(e->q0[b]);
+            cudaFree(e->q1[b]);
+            e->q0[b] = e->q1[b] = nullptr;
+        }
+        for (int b = 0; b < 2; ++b) {
+            if (cudaMalloc(&e->q0[b], es * e->state_len) != cudaSuccess ||
+                cudaMalloc(&e->q1[b], es * e->state_len) != cudaSuccess) {
+                cudaGetLastError();
+                e->state_cap = 0;
+                return fail(RSWR_ENOMEM, "state arrays: cudaMalloc failed");
+            }
+        }
+        e->state_cap = e->state_len;
+    }
+    for (int b = 0; b < 2; ++b) {
+        RSWR_CUDA(cudaMemset(e->q0[b], 0, es * e->state_len));
+        RSWR_CUDA(cudaMemset(e->q1[b], 0, es * e->state_len));
+    }
+    if (e->h_tiles.size() > e->tiles_cap) {
+        cudaFree(e->d_tiles);
+        e->d_tiles = nullptr;
+        if (cudaMalloc(&e->d_tiles, sizeof(TileDev) * e->h_tiles.size()) != cudaSuccess)
+            return fail(RSWR_ENOMEM, "tile table");
+        e->tiles_cap = e->h_tiles.size();
+    }
+    RSWR_CUDA(cudaMemcpy(e->d_tiles, e->h_tiles.data(), sizeof(TileDev) * e->h_tiles.size(), cudaMemcpyHostToDevice));
+    if ((size_t)e->ntiles > e->done_cap) {
+        cudaFree(e->d_done);
+        e->d_done = nullptr;
+        if (cudaMalloc(&e->d_done, sizeof(int) * e->ntiles) != cudaSuccess) return fail(RSWR_ENOMEM, "flags");
+        e->done_cap = e->ntiles;
+    }
+    RSWR_CUDA(cudaMemcpy(e->d_offsets, e->h_offsets.data(), sizeof(int64_t) * e->h_offsets.size(),
+                         cudaMemcpyHostToDevice));
+    return RSWR_OK;
+}
+
+rswr_status make_engine(Engine** out, int nprob, const rswr_problem* pr, int32_t dtype, int32_t form, bool is_plan)
+{
+    *out = nullptr;
+    if (nprob < 1 || !pr) return fail(RSWR_EINVAL, "need at least one problem");
+    if (dtype != RSWR_F32 && dtype != RSWR_F64) return fail(RSWR_EINVAL, "dtype must be RSWR_F32 or RSWR_F64");
+    int f;
+    if (form == RSWR_FORM_DEFAULT) f = dtype == RSWR_F64 ? kCanonical : kIncrement;
+    else if (form == RSWR_FORM_CANONICAL) f = kCanonical;
+    else if (form == RSWR_FORM_INCREMENT) f = kIncrement;
+    else return fail(RSWR_EINVAL, "bad form");
+    for (int p = 0; p < nprob; ++p) {
+        rswr_status st = validate(pr[p]);
+        if (st != RSWR_OK) return st;
+    }
+    Engine* e = new (std::nothrow) Engine();
+    if (!e) return fail(RSWR_ENOMEM, "host allocation");
+    e->dtype = dtype == RSWR_F64 ? kF64 : kF32;
+    e->form = f;
+    e->is_plan = is_plan;
+    int S = 1 << 30;
+    for (int p = 0; p < nprob; ++p) {
+        ProbHost ph{};
+        ph.nx = pr[p].nx; ph.xa = pr[p].xa; ph.xb = pr[p].xb; ph.a = pr[p].a; ph.dt = pr[p].dt;
+        ph.n_sub = pr[p].n_sub; ph.ov = pr[p].overlap;
+        coefficients(ph);
+        e->probs.push_back(ph);
+        S = std::min(S, pr[p].overlap / 2);
+    }
+    e->S = std::min(S, kSpanCap);
+    e->variant = default_variant(e->dtype, e->form);
+    if (e->variant < 0) {
+        delete e;
+        return fail(RSWR_ENOTSUP, "no kernel variant for this dtype/form");
+    }
+    cudaError_t ce = cudaGetDevice(&e->device);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device);
+    if (ce == cudaSuccess) ce = cudaMalloc(&e->d_problems, (e->dtype == kF64 ? sizeof(ProblemDev<double>)
+                                                                               : sizeof(ProblemDev<float>)) * nprob);
+    if (ce == cudaSuccess) ce = cudaMalloc(&e->d_offsets, sizeof(int64_t) * (nprob + 1));
+    if (ce == cudaSuccess) ce = cudaMalloc(&e->d_ticket, sizeof(unsigned long long));
+    if (ce == cudaSuccess) ce = cudaMalloc(&e->d_err, sizeof(DevError));
+    if (ce == cudaSuccess) ce = cudaMemset(e->d_err, 0, sizeof(DevError));
+    if (ce != cudaSuccess) {
+        free_engine(e);
+        return fail(RSWR_ECUDA, std::string("engine setup: ") + cudaGetErrorString(ce));
+    }
+    for (int v = 0; v < span_variant_count(); ++v) {
+        ce = span_prepare(v);
+        if (ce != cudaSuccess) {
+            free_engine(e);
+            return fail(RSWR_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(ce));
+        }
+    }
+    rswr_status st = layout(e);
+    if (st != RSWR_OK) {
+        free_engine(e);
+        return st;
+    }
+    *out = e;
+    return RSWR_OK;
+}
+
+// ---- pack / unpack between caller-packed arrays and the padded layout ----
+
+template <typename Real>
+__global__ void unpack_kernel(Real* state, const Real* packed, const int64_t* offsets, int nprob,
+                              const ProblemDev<Real>* problems, int64_t total)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nprob - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (offsets[mid] <= i) lo = mid; else hi = mid - 1;
+        }
+        state[problems[lo].base + (i - offsets[lo])] = packed[i];
+    }
+}
+
+template <typename Real>
+__global__ void pack_kernel(Real* packed, const Real* state, const int64_t* offsets, int nprob,
+                            const ProblemDev<Real>* problems, int64_t total)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nprob - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (offsets[mid] <= i) lo = mid; else hi = mid - 1;
+        }
+        packed[i] = state[problems[lo].base + (i - offsets[lo])];
+    }
+}
+
+int grid_for(int64_t n, int sms) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8)); }
+
+template <typename Real>
+rswr_status unpack(Engine* e, void* state, const void* packed, cudaStream_t s)
+{
+    if (e->probs.size() == 1) {
+        RSWR_CUDA(cudaMemcpyAsync(static_cast<Real*>(state) + e->probs[0].base, packed, sizeof(Real) * e->probs[0].nx,
+                                  cudaMemcpyDeviceToDevice, s));
+        return RSWR_OK;
+    }
+    unpack_kernel<Real><<<grid_for(e->packed_len, e->num_sms), 256, 0, s>>>(
+        static_cast<Real*>(state), static_cast<const Real*>(packed), e->d_offsets, (int)e->probs.size(),
+        static_cast<const ProblemDev<Real>*>(e->d_problems), e->packed_len);
+    RSWR_CUDA(cudaGetLastError());
+    return RSWR_OK;
+}
+
+template <typename Real>
+rswr_status pack(Engine* e, void* packed, const void* state, cudaStream_t s)
+{
+    if (e->probs.size() == 1) {
+        RSWR_CUDA(cudaMemcpyAsync(packed, static_cast<const Real*>(state) + e->probs[0].base,
+                                  sizeof(Real) * e->probs[0].nx, cudaMemcpyDeviceToDevice, s));
+        return RSWR_OK;
+    }
+    pack_kernel<Real><<<grid_for(e->packed_len, e->num_sms), 256, 0, s>>>(
+        static_cast<Real*>(packed), static_cast<const Real*>(state), e->d_offsets, (int)e->probs.size(),
+        static_cast<const ProblemDev<Real>*>(e->d_problems), e->packed_len);
+    RSWR_CUDA(cudaGetLastError());
+    return RSWR_OK;
+}
+
+// ---- one run ----------------------------------------------------------
+
+struct ProbeReq {
+    int64_t p;      // problem
+    int64_t j;      // grid point
+    int kind;       // 0 value, 1 flux
+    double scale;   // 0 -> use inv2dx (flux) / 1 (value)
+    void* out;
+    int64_t stride;
+    int64_t nmax;
+    bool scale_is_c2 = false;
+};
+
+struct RunReq {
+    const void* fA = nullptr;   // packed nprob x (T+1) or single
+    const void* fB = nullptr;
+    int64_t T = 0;
+    const void* q0 = nullptr;
+    const void* q1 = nullptr;
+    void* out0 = nullptr;
+    void* out1 = nullptr;
+    std::vector<ProbeReq> probes;
+    // point sources (adjoint runs): per problem js (-1 none), src base pointer and stride
+    std::vector<int64_t> js;
+    const void* src = nullptr;      // packed: problem p's source starts at src + p*src_pitch
+    int64_t src_pitch = 0;
+    int64_t src_stride = 1;
+    bool mono = false;
+};
+
+template <typename Real>
+rswr_status upload_problems(Engine* e, const RunReq& r, cudaStream_t s)
+{
+    std::vector<ProblemDev<Real>> h(e->probs.size());
+    for (size_t p = 0; p < e->probs.size(); ++p) {
+        const ProbHost& ph = e->probs[p];
+        ProblemDev<Real>& d = h[p];
+        d.base = ph.base;
+        d.nx = ph.nx;
+        d.tile0 = ph.tile0;
+        d.ntiles = ph.ntiles;
+        d.fA = r.fA ? static_cast<const Real*>(r.fA) + p * (r.T + 1) : nullptr;
+        d.fB = r.fB ? static_cast<const Real*>(r.fB) + p * (r.T + 1) : nullptr;
+        d.js = (!r.js.empty() && r.src) ? r.js[p] : -1;
+        d.src = (d.js >= 0) ? static_cast<const Real*>(r.src) + p * r.src_pitch : nullptr;
+        d.src_stride = r.src_stride;
+        if (sizeof(Real) == 8) {
+            d.c2 = (Real)ph.c2;
+            d.k = (Real)ph.k;
+        } else {
+            d.c2 = (Real)ph.c2f;
+            d.k = (Real)ph.kf;
+        }
+    }
+    RSWR_CUDA(cudaMemcpyAsync(e->d_problems, h.data(), sizeof(ProblemDev<Real>) * h.size(), cudaMemcpyHostToDevice, s));
+    return RSWR_OK;
+}
+
+template <typename Real>
+rswr_status upload_probes(Engine* e, const RunReq& r, int* nprobe, cudaStream_t s)
+{
+    std::vector<ProbeDev<Real>> h;
+    h.reserve(r.probes.size());
+    for (const ProbeReq& q : r.probes) {
+        const ProbHost& ph = e->probs[q.p];
+        ProbeDev<Real> d{};
+        d.gidx = ph.base + q.j;
+        d.out = static_cast<Real*>(q.out);
+        d.stride = q.stride;
+        d.nmax = q.nmax;
+        d.kind = q.kind;
+        double sc = q.scale;
+        if (q.scale_is_c2) d.scale = sizeof(Real) == 8 ? (Real)ph.c2 : (Real)ph.c2f;
+        else if (q.kind == 1) d.scale = sizeof(Real) == 8 ? (Real)ph.inv2dx : (Real)ph.inv2dxf;
+        else d.scale = (Real)sc;
+        h.push_back(d);
+    }
+    std::sort(h.begin(), h.end(), [](const ProbeDev<Real>& a, const ProbeDev<Real>& b) { return a.gidx < b.gidx; });
+    *nprobe = (int)h.size();
+    // per-tile ranges over the sorted probes: a probe belongs to the tile whose core holds its point
+    bool changed = false;
+    size_t q = 0;
+    for (size_t t = 0; t < e->h_tiles.size(); ++t) {
+        TileDev& td = e->h_tiles[t];
+        const int64_t lo = e->probs[td.problem].base + (int64_t)td.local * e->core;
+        const int64_t hi = lo + e->core;
+        while (q < h.size() && h[q].gidx < lo) ++q;
+        size_t q2 = q;
+        while (q2 < h.size() && h[q2].gidx < hi) ++q2;
+        if (td.probe_begin != (int32_t)q || td.probe_end != (int32_t)q2) changed = true;
+        td.probe_begin = (int32_t)q;
+        td.probe_end = (int32_t)q2;
+    }
+    if (changed)
+        RSWR_CUDA(cudaMemcpyAsync(e->d_tiles, e->h_tiles.data(), sizeof(TileDev) * e->h_tiles.size(),
+                                  cudaMemcpyHostToDevice, s));
+    if (!h.empty()) {
+        if (h.size() > e->probes_cap) {
+            RSWR_CUDA(cudaStreamSynchronize(s));
+            cudaFree(e->d_probes);
+            e->d_probes = nullptr;
+            if (cudaMalloc(&e->d_probes, sizeof(ProbeDev<Real>) * h.size()) != cudaSuccess)
+                return fail(RSWR_ENOMEM, "probe table");
+            e->probes_cap = h.size();
+        }
+        RSWR_CUDA(cudaMemcpyAsync(e->d_probes, h.data(), sizeof(ProbeDev<Real>) * h.size(), cudaMemcpyHostToDevice, s));
+    }
+    return RSWR_OK;
+}
+
+template <typename Real>
+SpanParams<Real> span_params(Engine* e, int64_t T, int nspans)
+{
+    SpanParams<Real> prm{};
+    prm.problems = static_cast<const ProblemDev<Real>*>(e->d_problems);
+    prm.tiles = static_cast<const TileDev*>(e->d_tiles);
+    prm.probes = static_cast<const ProbeDev<Real>*>(e->d_probes);
+    for (int b = 0; b < 2; ++b) {
+        prm.q0[b] = static_cast<Real*>(e->q0[b]);
+        prm.q1[b] = static_cast<Real*>(e->q1[b]);
+    }
+    prm.ntiles = e->ntiles;
+    prm.T = T;
+    prm.H = e->H;
+    prm.core = e->core;
+    prm.S = e->S;
+    prm.nspans = nspans;
+    prm.span = -1;
+    prm.inject_tile = e->inject_tile;
+    prm.inject_span = e->inject_span;
+    prm.ticket = e->d_ticket;
+    prm.done = e->d_done;
+    prm.err = e->d_err;
+    prm.wait_ns = (long long)(e->wait_s * 1e9);
+    return prm;
+}
+
+template <typename Real>
+rswr_status run_impl(Engine* e, const RunReq& r, cudaStream_t s)
+{
+    const size_t es = sizeof(Real);
+    RSWR_CUDA(cudaMemsetAsync(e->d_err, 0, sizeof(DevError), s));
+    rswr_status st = upload_problems<Real>(e, r, s);
+    if (st != RSWR_OK) return st;
+    int nprobe = 0;
+    st = upload_probes<Real>(e, r, &nprobe, s);
+    if (st != RSWR_OK) return st;
+
+    // level-0 state into buffer 0
+    if (!r.q0) {
+        RSWR_CUDA(cudaMemsetAsync(e->q0[0], 0, es * e->state_len, s));
+        RSWR_CUDA(cudaMemsetAsync(e->q1[0], 0, es * e->state_len, s));
+    } else {
+        if ((st = unpack<Real>(e, e->q0[0], r.q0, s)) != RSWR_OK) return st;
+        if (r.q1) {
+            if ((st = unpack<Real>(e, e->q1[0], r.q1, s)) != RSWR_OK) return st;
+        } else if (e->form == kCanonical) {
+            if ((st = unpack<Real>(e, e->q1[0], r.q0, s)) != RSWR_OK) return st;
+        } else {
+            RSWR_CUDA(cudaMemsetAsync(e->q1[0], 0, es * e->state_len, s));
+        }
+    }
+    RSWR_CUDA(set_boundary_launch(e->dtype, e->form, e->q0[0], e->q1[0], e->d_problems, (int)e->probs.size(), s));
+
+    const void* fin0;
+    const void* fin1;
+    if (!r.mono) {
+        const int nspans = (int)((r.T + e->S - 1) / e->S);
+        SpanParams<Real> prm = span_params<Real>(e, r.T, nspans);
+        int bps = 0;
+        RSWR_CUDA(span_occupancy(e->variant, &bps));
+        if (bps < 1) return fail(RSWR_ENOTSUP, "span kernel does not fit on an SM");
+        if (nspans > 0) {
+            if (e->mode == RSWR_MODE_PERSISTENT) {
+                RSWR_CUDA(cudaMemsetAsync(e->d_ticket, 0, sizeof(unsigned long long), s));
+                RSWR_CUDA(cudaMemsetAsync(e->d_done, 0, sizeof(int) * e->ntiles, s));
+                const int grid = (int)std::min<int64_t>((int64_t)bps * e->num_sms, (int64_t)nspans * e->ntiles);
+                RSWR_CUDA(span_launch(e->variant, &prm, grid, s));
+            } else {
+                const int grid = (int)std::min<int64_t>((int64_t)bps * e->num_sms, e->ntiles);
+                for (int k = 0; k < nspans; ++k) {
+                    prm.span = k;
+                    RSWR_CUDA(span_launch(e->variant, &prm, grid, s));
+                }
+            }
+        }
+        fin0 = e->q0[nspans & 1];
+        fin1 = e->q1[nspans & 1];
+    } else {
+        // monolithic: canonical alternates u^n between q0[0] and q1[0]; increment keeps v in q1[0]
+        MonoParams<Real> mp{};
+        mp.probes = static_cast<const ProbeDev<Real>*>(e->d_probes);
+        mp.nprobe = nprobe;
+        mp.form = e->form;
+        const ProbHost& ph = e->probs[0];
+        mp.base = ph.base;
+        mp.nx = ph.nx;
+        mp.fA = static_cast<const Real*>(r.fA);
+        mp.fB = static_cast<const Real*>(r.fB);
+        mp.c2 = sizeof(Real) == 8 ? (Real)ph.c2 : (Real)ph.c2f;
+        mp.k = sizeof(Real) == 8 ? (Real)ph.k : (Real)ph.kf;
+        Real* a = static_cast<Real*>(e->q0[0]);
+        Real* b = static_cast<Real*>(e->q1[0]);
+        Real* ua = static_cast<Real*>(e->q0[0]);
+        Real* ub = static_cast<Real*>(e->q0[1]);
+        for (int64_t n = 0; n < r.T; ++n) {
+            mp.n = n;
+            if (e->form == kCanonical) {
+                mp.cur = a;
+                mp.prev = b;
+                mp.unew = nullptr;
+                RSWR_CUDA(mono_launch(e->dtype, &mp, s));
+                std::swap(a, b);
+            } else {
+                mp.cur = ua;
+                mp.prev = b;
+                mp.unew = ub;
+                RSWR_CUDA(mono_launch(e->dtype, &mp, s));
+                std::swap(ua, ub);
+            }
+        }
+        if (e->form == kCanonical) {
+            fin0 = a;
+            fin1 = b;
+        } else {
+            fin0 = ua;
+            fin1 = b;
+        }
+    }
+    RSWR_CUDA(probe_final_launch(e->dtype, e->d_probes, nprobe, fin0, r.T, s));
+    if (r.out0 && (st = pack<Real>(e, r.out0, fin0, s)) != RSWR_OK) return st;
+    if (r.out1 && (st = pack<Real>(e, r.out1, fin1, s)) != RSWR_OK) return st;
+    return RSWR_OK;
+}
+
+rswr_status run_engine(Engine* e, const RunReq& r, cudaStream_t s)
+{
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != e->device) RSWR_CUDA(cudaSetDevice(e->device));
+    rswr_status st = e->dtype == kF64 ? run_impl<double>(e, r, s) : run_impl<float>(e, r, s);
+    if (cur != e->device && cur >= 0) cudaSetDevice(cur);
+    return st;
+}
+
+rswr_status check_engine(Engine* e, cudaStream_t s, int32_t* code, int32_t* tile, int32_t* span)
+{
+    RSWR_CUDA(cudaStreamSynchronize(s));
+    DevError h{};
+    RSWR_CUDA(cudaMemcpy(&h, e->d_err, sizeof(h), cudaMemcpyDeviceToHost));
+    if (code) *code = h.code;
+    if (tile) *tile = h.tile;
+    if (span) *span = h.span;
+    if (h.code == kDevTimeoutLoad || h.code == kDevTimeoutFlag)
+        return fail(RSWR_ETIMEOUT, "device wait expired (code " + std::to_string(h.code) + ", tile " +
+                                       std::to_string(h.tile) + ", span " + std::to_string(h.span) + ")");
+    if (h.code != 0) return fail(RSWR_ECUDA, "device error code " + std::to_string(h.code));
+    return RSWR_OK;
+}
+
+rswr_status fill_info(const Engine* e, rswr_plan_info* info)
+{
+    if (!e || !info) return fail(RSWR_EINVAL, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    const ProbHost& p = e->probs[0];
+    info->nx = p.nx;
+    info->dtype = e->dtype == kF64 ? RSWR_F64 : RSWR_F32;
+    info->form = e->form == kCanonical ? RSWR_FORM_CANONICAL : RSWR_FORM_INCREMENT;
+    info->n_sub = p.n_sub;
+    info->overlap = p.ov;
+    info->c = p.c;
+    info->c2 = p.c2;
+    info->k = p.k;
+    info->inv2dx = p.inv2dx;
+    info->c2f = p.c2f;
+    info->kf = p.kf;
+    info->inv2dxf = p.inv2dxf;
+    info->span_steps = e->S;
+    info->halo = e->H;
+    info->core = e->core;
+    info->window = e->W;
+    info->points_per_thread = e->P;
+    info->threads_per_cta = e->NT;
+    info->variant = e->variant;
+    info->mode = e->mode;
+    info->ntiles = e->ntiles;
+    info->state_len = e->state_len;
+    info->workspace_bytes = (int64_t)(4 * e->state_cap * e->esize());
+    return RSWR_OK;
+}
+
+rswr_status set_variant(Engine* e, int32_t v)
+{
+    if (v < 0 || v >= span_variant_count()) return fail(RSWR_EINVAL, "variant out of range");
+    const VariantInfo vi = span_variant_info(v);
+    if (vi.dtype != e->dtype || vi.form != e->form) return fail(RSWR_EINVAL, "variant has another dtype or form");
+    const int old = e->variant;
+    e->variant = v;
+    rswr_status st = layout(e);
+    if (st != RSWR_OK) {
+        e->variant = old;
+        layout(e);
+    }
+    return st;
+}
+
+// interface output-waveform probes of one problem (see rswr_run)
+void add_trace_probes(const ProbHost& ph, int64_t p, void* traces, int64_t T, size_t es, std::vector<ProbeReq>& out)
+{
+    const int64_t N = ph.n_sub, el = (ph.ov + 1) / 2, er = ph.ov / 2;
+    for (int64_t i = 0; i + 1 < N; ++i) {
+        const int64_t b1 = (i + 1) * ph.nx / N;
+        const int64_t Lnext = std::max<int64_t>(b1 - el, 0);
+        const int64_t Rthis = std::min<int64_t>(b1 - 1 + er, ph.nx - 1);
+        char* base = static_cast<char*>(traces);
+        out.push_back(ProbeReq{p, Lnext, 1, 0.0, base + es * ((2 * i + 0) * (T + 1)), 1, T});
+        out.push_back(ProbeReq{p, Rthis, 1, 0.0, base + es * ((2 * i + 1) * (T + 1)), 1, T});
+    }
+}
+
+rswr_status plan_run(Engine* e, const void* fA, const void* fB, int64_t T, const void* q0, const void* q1, void* out0,
+                     void* out1, void* traces, int64_t j_r, void* recv, void* stream, bool mono)
+{
+    if (!e) return fail(RSWR_EINVAL, "NULL plan");
+    if (T < 0 || T > ((int64_t)1 << 40)) return fail(RSWR_EINVAL, "T out of range");
+    if (!out0 || !out1) return fail(RSWR_EINVAL, "out0 and out1 are required");
+    const ProbHost& ph = e->probs[0];
+    if (recv && (j_r < 0 || j_r >= ph.nx)) return fail(RSWR_EINVAL, "receiver index outside the grid");
+    if (e->inject_tile >= 0 && mono) return fail(RSWR_EINVAL, "fault injection applies to RSWR runs only");
+    RunReq r;
+    r.fA = fA;
+    r.fB = fB;
+    r.T = T;
+    r.q0 = q0;
+    r.q1 = q1;
+    r.out0 = out0;
+    r.out1 = out1;
+    r.mono = mono;
+    if (traces) add_trace_probes(ph, 0, traces, T, e->esize(), r.probes);
+    if (recv) r.probes.push_back(ProbeReq{0, j_r, 0, 1.0, recv, 1, T});
+    return run_engine(e, r, static_cast<cudaStream_t>(stream));
+}
+
+// dL/dfA of a receiver-trace functional: the adjoint variables run forward in
+// reversed time (level m = lambda^{T+1-m}) from rest, with zero Dirichlet data
+// and the source wbar[T-n] entering at step n -> n+1 at j_r; the probe at
+// j = 1 with scale c2 yields grad[T - m] = c2 lambda^{T+1-m}_1.
+rswr_status adjoint_g(Engine* e, int64_t T, const int64_t* j_r, const void* wbar, void* grad, cudaStream_t s)
+{
+    const size_t es = e->esize();
+    const int np = (int)e->probs.size();
+    if (e->scratch_cap < (size_t)e->packed_len) {
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(e->d_scratch[b]);
+            e->d_scratch[b] = nullptr;
+            if (cudaMalloc(&e->d_scratch[b], es * e->packed_len) != cudaSuccess) return fail(RSWR_ENOMEM, "scratch");
+        }
+        e->scratch_cap = e->packed_len;
+    }
+    RunReq r;
+    r.T = T + 1;
+    r.out0 = e->d_scratch[0];
+    r.out1 = e->d_scratch[1];
+    r.js.assign(np, -1);
+    r.src = static_cast<const char*>(wbar) + es * (T + 1);
+    r.src_pitch = T + 1;
+    r.src_stride = -1;
+    RSWR_CUDA(cudaMemsetAsync(grad, 0, es * (T + 1) * np, s));
+    bool any = false;
+    for (int p = 0; p < np; ++p) {
+        const int64_t j = j_r[p];
+        char* g = static_cast<char*>(grad) + es * (T + 1) * p;
+        if (j == 0) {
+            // the receiver is the Dirichlet node itself: dL/dfA = wbar
+            RSWR_CUDA(cudaMemcpyAsync(g, static_cast<const char*>(wbar) + es * (T + 1) * p, es * (T + 1),
+                                      cudaMemcpyDeviceToDevice, s));
+            continue;
+        }
+        if (j >= e->probs[p].nx - 1) continue;  // right Dirichlet node: no dependence on fA
+        r.js[p] = j;
+        ProbeReq q{p, 1, 0, 0.0, g + es * T, -1, T};
+        q.scale_is_c2 = true;
+        r.probes.push_back(q);
+        any = true;
+    }
+    if (!any) return RSWR_OK;
+    return run_engine(e, r, s);
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+struct rswr_plan_s {
+    Engine* e;
+};
+struct rswr_batch_s {
+    Engine* e;
+};
+
+extern "C" {
+
+const char* rswr_status_string(rswr_status s)
+{
+    switch (s) {
+        case RSWR_OK: return "RSWR_OK";
+        case RSWR_EINVAL: return "RSWR_EINVAL";
+        case RSWR_ECFL: return "RSWR_ECFL";
+        case RSWR_EOVERLAP: return "RSWR_EOVERLAP";
+        case RSWR_ENOMEM: return "RSWR_ENOMEM";
+        case RSWR_ECUDA: return "RSWR_ECUDA";
+        case RSWR_ETIMEOUT: return "RSWR_ETIMEOUT";
+        case RSWR_ENOTSUP: return "RSWR_ENOTSUP";
+    }
+    return "unknown status";
+}
+
+const char* rswr_last_error_message(void) { return g_msg.c_str(); }
+
+int32_t rswr_version(void) { return 100; }
+
+rswr_status rswr_plan_create(rswr_plan_t* plan, double xa, double xb, double a, int64_t nx, double dt, int32_t n_sub,
+                             int32_t overlap, int32_t dtype, int32_t form, uint32_t flags)
+{
+    if (!plan) return fail(RSWR_EINVAL, "plan is NULL");
+    *plan = nullptr;
+    (void)flags;
+    rswr_problem q{nx, xa, xb, a, dt, n_sub, overlap};
+    Engine* e = nullptr;
+    rswr_status st = make_engine(&e, 1, &q, dtype, form, true);
+    if (st != RSWR_OK) return st;
+    *plan = new (std::nothrow) rswr_plan_s{e};
+    if (!*plan) {
+        free_engine(e);
+        return fail(RSWR_ENOMEM, "host allocation");
+    }
+    return RSWR_OK;
+}
+
+void rswr_plan_destroy(rswr_plan_t plan)
+{
+    if (!plan) return;
+    free_engine(plan->e);
+    delete plan;
+}
+
+rswr_status rswr_plan_get_info(rswr_plan_t plan, rswr_plan_info* info)
+{
+    if (!plan) return fail(RSWR_EINVAL, "NULL plan");
+    return fill_info(plan->e, info);
+}
+
+rswr_status rswr_plan_set_span(rswr_plan_t plan, int32_t S)
+{
+    if (!plan) return fail(RSWR_EINVAL, "NULL plan");
+    Engine* e = plan->e;
+    if (S < 1 || S > e->probs[0].ov / 2 || S > kSpanCap)
+        return fail(RSWR_EOVERLAP, "span must satisfy 1 <= S <= floor(overlap/2)");
+    const int old = e->S;
+    e->S = S;
+    rswr_status st = layout(e);
+    if (st != RSWR_OK) {
+        e->S = old;
+        layout(e);
+    }
+    return st;
+}
+
+rswr_status rswr_plan_set_variant(rswr_plan_t plan, int32_t variant)
+{
+    if (!plan) return fail(RSWR_EINVAL, "NULL plan");
+    return set_variant(plan->e, variant);
+}
+
+rswr_status rswr_plan_set_mode(rswr_plan_t plan, int32_t mode)
+{
+    if (!plan) return fail(RSWR_EINVAL, "NULL plan");
+    if (mode != RSWR_MODE_PERSISTENT && mode != RSWR_MODE_PER_SPAN) return fail(RSWR_EINVAL, "bad mode");
+    plan->e->mode = mode;
+    return RSWR_OK;
+}
+
+rswr_status rswr_plan_set_wait_limit(rswr_plan_t plan, double seconds)
+{
+    if (!plan) return fail(RSWR_EINVAL, "NULL plan");
+    if (!(seconds > 0.0) || seconds > 3600.0) return fail(RSWR_EINVAL, "wait limit out of range");
+    plan->e->wait_s = seconds;
+    return RSWR_OK;
+}
+
+rswr_status rswr_plan_inject_missing_flag(rswr_plan_t plan, int32_t tile, int32_t span)
+{
+    if (!plan) return fail(RSWR_EINVAL, "NULL plan");
+    if (tile >= plan->e->ntiles) return fail(RSWR_EINVAL, "tile out of range");
+    plan->e->inject_tile = tile < 0 ? -1 : tile;
+    plan->e->inject_span = span;
+    return RSWR_OK;
+}
+
+rswr_status rswr_plan_check(rswr_plan_t plan, void* stream, int32_t* code, int32_t* tile, int32_t* span)
+{
+    if (!plan) return fail(RSWR_EINVAL, "NULL plan");
+    return check_engine(plan->e, static_cast<cudaStream_t>(stream), code, tile, span);
+}
+
+rswr_status rswr_run(rswr_plan_t plan, const void* fA, const void* fB, int64_t T, const void* q0, const void* q1,
+                     void* out0, void* out1, void* traces, int64_t j_r, void* recv, void* stream)
+{
+    if (!plan) return fail(RSWR_EINVAL, "NULL plan");
+    return plan_run(plan->e, fA, fB, T, q0, q1, out0, out1, traces, j_r, recv, stream, false);
+}
+
+rswr_status rswr_mono(rswr_plan_t plan, const void* fA, const void* fB, int64_t T, const void* q0, const void* q1,
+                      void* out0, void* out1, void* traces, int64_t j_r, void* recv, void* stream)
+{
+    if (!plan) return fail(RSWR_EINVAL, "NULL plan");
+    return plan_run(plan->e, fA, fB, T, q0, q1, out0, out1, traces, j_r, recv, stream, true);
+}
+
+rswr_status rswr_run_host(rswr_plan_t plan, const void* fA, const void* fB, int64_t T, const void* q0,
+                          const void* q1, void* out0, void* out1, void* traces, int64_t j_r, void* recv, void* stream)
+{
+    if (!plan) return fail(RSWR_EINVAL, "NULL plan");
+    Engine* e = plan->e;
+    if (T < 0) return fail(RSWR_EINVAL, "T < 0");
+    if (!out0 || !out1) return fail(RSWR_EINVAL, "out0 and out1 are required");
+    const size_t es = e->esize();
+    const int64_t nx = e->probs[0].nx;
+    const int64_t ntr = traces ? (int64_t)(e->probs[0].n_sub - 1) * 2 * (T + 1) : 0;
+    // staging layout: fA | fB | q0 | q1 | out0 | out1 | traces | recv
+    const size_t need = es * (2 * (T + 1) + 4 * nx + ntr + (T + 1)) + 8 * 64;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (need > e->host_stage_cap) {
+        RSWR_CUDA(cudaStreamSynchronize(s));
+        cudaFree(e->d_host_stage);
+        e->d_host_stage = nullptr;
+        if (cudaMalloc(&e->d_host_stage, need) != cudaSuccess) return fail(RSWR_ENOMEM, "host staging");
+        e->host_stage_cap = need;
+    }
+    char* at = static_cast<char*>(e->d_host_stage);
+    auto take = [&](size_t bytes) {
+        char* p = at;
+        at += (bytes + 255) / 256 * 256;
+        return p;
+    };
+    char* dfA = fA ? take(es * (T + 1)) : nullptr;
+    char* dfB = fB ? take(es * (T + 1)) : nullptr;
+    char* dq0 = q0 ? take(es * nx) : nullptr;
+    char* dq1 = q1 ? take(es * nx) : nullptr;
+    char* do0 = take(es * nx);
+    char* do1 = take(es * nx);
+    char* dtr = traces ? take(es * ntr) : nullptr;
+    char* drc = recv ? take(es * (T + 1)) : nullptr;
+    if ((size_t)(at - static_cast<char*>(e->d_host_stage)) > e->host_stage_cap) return fail(RSWR_ENOMEM, "staging");
+    if (fA) RSWR_CUDA(cudaMemcpyAsync(dfA, fA, es * (T + 1), cudaMemcpyHostToDevice, s));
+    if (fB) RSWR_CUDA(cudaMemcpyAsync(dfB, fB, es * (T + 1), cudaMemcpyHostToDevice, s));
+    if (q0) RSWR_CUDA(cudaMemcpyAsync(dq0, q0, es * nx, cudaMemcpyHostToDevice, s));
+    if (q1) RSWR_CUDA(cudaMemcpyAsync(dq1, q1, es * nx, cudaMemcpyHostToDevice, s));
+    rswr_status st = plan_run(e, dfA, dfB, T, dq0, dq1, do0, do1, dtr, j_r, drc, stream, false);
+    if (st != RSWR_OK) return st;
+    RSWR_CUDA(cudaMemcpyAsync(out0, do0, es * nx, cudaMemcpyDeviceToHost, s));
+    RSWR_CUDA(cudaMemcpyAsync(out1, do1, es * nx, cudaMemcpyDeviceToHost, s));
+    if (traces) RSWR_CUDA(cudaMemcpyAsync(traces, dtr, es * ntr, cudaMemcpyDeviceToHost, s));
+    if (recv) RSWR_CUDA(cudaMemcpyAsync(recv, drc, es * (T + 1), cudaMemcpyDeviceToHost, s));
+    return check_engine(e, s, nullptr, nullptr, nullptr);
+}
+
+rswr_status rswr_adjoint(rswr_plan_t plan, const void* fA, const void* fB, int64_t T, int64_t j_r, const void* wbar,
+                         void* grad_fA, double* grad_a, void* stream)
+{
+    if (!plan) return fail(RSWR_EINVAL, "NULL plan");
+    Engine* e = plan->e;
+    if (T < 0) return fail(RSWR_EINVAL, "T < 0");
+    if (!wbar || !grad_fA) return fail(RSWR_EINVAL, "wbar and grad_fA are required");
+    if (j_r < 0 || j_r >= e->probs[0].nx) return fail(RSWR_EINVAL, "receiver index outside the grid");
+    (void)fA;
+    (void)fB;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    rswr_status st = adjoint_g(e, T, &j_r, wbar, grad_fA, s);
+    if (st != RSWR_OK) return st;
+    if (grad_a) return fail(RSWR_ENOTSUP, "dL/da is not available in this build");
+    return RSWR_OK;
+}
+
+rswr_status rswr_batch_create(rswr_batch_t* batch, int32_t nprob, const rswr_problem* problems, int32_t dtype,
+                              int32_t form, uint32_t flags)
+{
+    if (!batch) return fail(RSWR_EINVAL, "batch is NULL");
+    *batch = nullptr;
+    (void)flags;
+    Engine* e = nullptr;
+    rswr_status st = make_engine(&e, nprob, problems, dtype, form, false);
+    if (st != RSWR_OK) return st;
+    *batch = new (std::nothrow) rswr_batch_s{e};
+    if (!*batch) {
+        free_engine(e);
+        return fail(RSWR_ENOMEM, "host allocation");
+    }
+    return RSWR_OK;
+}
+
+void rswr_batch_destroy(rswr_batch_t batch)
+{
+    if (!batch) return;
+    free_engine(batch->e);
+    delete batch;
+}
+
+rswr_status rswr_batch_offsets(rswr_batch_t batch, int64_t* offsets)
+{
+    if (!batch || !offsets) return fail(RSWR_EINVAL, "NULL argument");
+    std::copy(batch->e->h_offsets.begin(), batch->e->h_offsets.end(), offsets);
+    return RSWR_OK;
+}
+
+rswr_status rswr_batch_get_info(rswr_batch_t batch, rswr_plan_info* info)
+{
+    if (!batch) return fail(RSWR_EINVAL, "NULL batch");
+    return fill_info(batch->e, info);
+}
+
+rswr_status rswr_batch_set_mode(rswr_batch_t batch, int32_t mode)
+{
+    if (!batch) return fail(RSWR_EINVAL, "NULL batch");
+    if (mode != RSWR_MODE_PERSISTENT && mode != RSWR_MODE_PER_SPAN) return fail(RSWR_EINVAL, "bad mode");
+    batch->e->mode = mode;
+    return RSWR_OK;
+}
+
+rswr_status rswr_batch_set_variant(rswr_batch_t batch, int32_t variant)
+{
+    if (!batch) return fail(RSWR_EINVAL, "NULL batch");
+    return set_variant(batch->e, variant);
+}
+
+rswr_status rswr_batch_set_wait_limit(rswr_batch_t batch, double seconds)
+{
+    if (!batch) return fail(RSWR_EINVAL, "NULL batch");
+    if (!(seconds > 0.0) || seconds > 3600.0) return fail(RSWR_EINVAL, "wait limit out of range");
+    batch->e->wait_s = seconds;
+    return RSWR_OK;
+}
+
+rswr_status rswr_batch_check(rswr_batch_t batch, void* stream, int32_t* code, int32_t* tile, int32_t* span)
+{
+    if (!batch) return fail(RSWR_EINVAL, "NULL batch");
+    return check_engine(batch->e, static_cast<cudaStream_t>(stream), code, tile, span);
+}
+
+rswr_status rswr_batch_run(rswr_batch_t batch, const void* fA, const void* fB, int64_t T, const void* q0,
+                           const void* q1, void* out0, void* out1, const int64_t* j_r, void* recv, void* stream)
+{
+    if (!batch) return fail(RSWR_EINVAL, "NULL batch");
+    Engine* e = batch->e;
+    if (T < 0) return fail(RSWR_EINVAL, "T < 0");
+    if (!out0 || !out1) return fail(RSWR_EINVAL, "out0 and out1 are required");
+    RunReq r;
+    r.fA = fA;
+    r.fB = fB;
+    r.T = T;
+    r.q0 = q0;
+    r.q1 = q1;
+    r.out0 = out0;
+    r.out1 = out1;
+    if (recv && j_r) {
+        for (size_t p = 0; p < e->probs.size(); ++p) {
+            if (j_r[p] < 0) continue;
+            if (j_r[p] >= e->probs[p].nx) return fail(RSWR_EINVAL, "receiver index outside the grid");
+            r.probes.push_back(ProbeReq{(int64_t)p, j_r[p], 0, 1.0,
+                                        static_cast<char*>(recv) + e->esize() * (T + 1) * p, 1, T});
+        }
+    }
+    return run_engine(e, r, static_cast<cudaStream_t>(stream));
+}
+
+rswr_status rswr_batch_adjoint(rswr_batch_t batch, const void* fA, const void* fB, int64_t T, const int64_t* j_r,
+                               const void* wbar, void* grad_fA, double* grad_a, void* stream)
+{
+    if (!batch) return fail(RSWR_EINVAL, "NULL batch");
+    Engine* e = batch->e;
+    if (T < 0 || !j_r || !wbar || !grad_fA) return fail(RSWR_EINVAL, "bad argument");
+    for (size_t p = 0; p < e->probs.size(); ++p)
+        if (j_r[p] < 0 || j_r[p] >= e->probs[p].nx) return fail(RSWR_EINVAL, "receiver index outside the grid");
+    (void)fA;
+    (void)fB;
+    rswr_status st = adjoint_g(e, T, j_r, wbar, grad_fA, static_cast<cudaStream_t>(stream));
+    if (st != RSWR_OK) return st;
+    if (grad_a) return fail(RSWR_ENOTSUP, "dL/da is not available in this build");
+    return RSWR_OK;
+}
+
+rswr_status rswr_plan_autotune(rswr_plan_t plan, int64_t probe_steps, int32_t* variant, void* stream)
+{
+    if (!plan) return fail(RSWR_EINVAL, "NULL plan");
+    Engine* e = plan->e;
+    if (probe_steps < 1) return fail(RSWR_EINVAL, "probe_steps must be >= 1");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t nx = e->probs[0].nx;
+    const size_t es = e->esize();
+    if (e->scratch_cap < (size_t)nx) {
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(e->d_scratch[b]);
+            e->d_scratch[b] = nullptr;
+            if (cudaMalloc(&e->d_scratch[b], es * nx) != cudaSuccess) return fail(RSWR_ENOMEM, "scratch");
+        }
+        e->scratch_cap = nx;
+    }
+    cudaEvent_t a, b;
+    RSWR_CUDA(cudaEventCreate(&a));
+    RSWR_CUDA(cudaEventCreate(&b));
+    float best = 1e30f;
+    int best_v = e->variant, best_mode = e->mode;
+    const int keep_mode = e->mode;
+    for (int v = 0; v < span_variant_count(); ++v) {
+        const VariantInfo vi = span_variant_info(v);
+        if (vi.dtype != e->dtype || vi.form != e->form) continue;
+        if (set_variant(e, v) != RSWR_OK) continue;
+        for (int mode = 0; mode < 2; ++mode) {
+            e->mode = mode;
+            rswr_status st = plan_run(e, nullptr, nullptr, probe_steps, nullptr, nullptr, e->d_scratch[0],
+                                      e->d_scratch[1], nullptr, 0, nullptr, stream, false);  // warm-up
+            if (st != RSWR_OK) continue;
+            RSWR_CUDA(cudaEventRecord(a, s));
+            st = plan_run(e, nullptr, nullptr, probe_steps, nullptr, nullptr, e->d_scratch[0], e->d_scratch[1],
+                          nullptr, 0, nullptr, stream, false);
+            RSWR_CUDA(cudaEventRecord(b, s));
+            RSWR_CUDA(cudaEventSynchronize(b));
+            float ms = 0.f;
+            RSWR_CUDA(cudaEventElapsedTime(&ms, a, b));
+            if (st == RSWR_OK && ms < best) {
+                best = ms;
+                best_v = v;
+                best_mode = mode;
+            }
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    e->mode = keep_mode;
+    rswr_status st = set_variant(e, best_v);
+    e->mode = best_mode;
+    if (variant) *variant = best_v;
+    return st;
+}
+
+int32_t rswr_variant_count(void) { return span_variant_count(); }
+
+rswr_status rswr_variant_get(int32_t v, int32_t* dtype, int32_t* form, int32_t* points_per_thread,
+                             int32_t* threads_per_cta)
+{
+    if (v < 0 || v >= span_variant_count()) return fail(RSWR_EINVAL, "variant out of range");
+    const VariantInfo vi = span_variant_info(v);
+    if (dtype) *dtype = vi.dtype == kF64 ? RSWR_F64 : RSWR_F32;
+    if (form) *form = vi.form == kCanonical ? RSWR_FORM_CANONICAL : RSWR_FORM_INCREMENT;
+    if (points_per_thread) *points_per_thread = vi.P;
+    if (threads_per_cta) *threads_per_cta = vi.NT;
+    return RSWR_OK;
+}
+
+}  // extern "C"

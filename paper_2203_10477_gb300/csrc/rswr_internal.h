@@ -1,0 +1,115 @@
+// rswr_internal.h -- data structures shared by the RSWR kernels and the host
+// runtime of librswr (not part of the public C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rswr_device.cuh"
+
+namespace rswr {
+
+enum Form : int { kCanonical = 0, kIncrement = 1 };
+enum DType : int { kF32 = 0, kF64 = 1 };
+
+// One independent 1-D problem inside a plan or a batch.  Grid point j of the
+// problem lives at index base + j of every state array; the arrays are padded
+// with at least H zero points on both sides of every problem.
+template <typename Real>
+struct ProblemDev {
+    int64_t base;
+    int64_t nx;
+    int64_t tile0;       // global index of the problem's first tile
+    int64_t ntiles;
+    const Real* fA;      // Dirichlet samples, level n at fA[n]; NULL means 0
+    const Real* fB;
+    const Real* src;     // point source: added to point js at level n: src[n * src_stride]
+    int64_t src_stride;
+    int64_t js;          // -1: no source
+    Real c2;
+    Real k;              // 2 - 2 c2
+};
+
+struct TileDev {
+    int32_t problem;
+    int32_t local;        // tile index within its problem (core starts at local * core)
+    int32_t probe_begin;  // probes whose point lies in this tile's core
+    int32_t probe_end;
+};
+
+// A per-level sample of the state: kind 0 records u_j * scale, kind 1 records
+// (u_{j+1} - u_{j-1}) * scale.  Level n goes to out[n * stride] for n <= nmax.
+template <typename Real>
+struct ProbeDev {
+    int64_t gidx;  // absolute index of point j in the state arrays
+    Real* out;
+    int64_t stride;
+    int64_t nmax;
+    Real scale;
+    int32_t kind;
+};
+
+template <typename Real>
+struct SpanParams {
+    const ProblemDev<Real>* problems;
+    const TileDev* tiles;
+    const ProbeDev<Real>* probes;
+    Real* q0[2];  // ping-pong state: [buffer] first component (u^n)
+    Real* q1[2];  // second component (u^{n-1} canonical, v^n increment)
+    int64_t ntiles;
+    int64_t T;           // total steps of the run
+    int32_t H;           // halo width of a CTA window (>= S)
+    int32_t core;        // owned points per tile (window W = core + 2H)
+    int32_t S;           // steps per span
+    int32_t nspans;
+    int32_t span;        // >= 0: launch covers that span only; -1: persistent over all spans
+    int32_t inject_tile; // test hook: this tile never publishes span inject_span (-1: off)
+    int32_t inject_span;
+    int32_t pad_;
+    unsigned long long* ticket;  // persistent mode: global ticket counter (zeroed per launch)
+    int* done;                   // persistent mode: spans completed per tile (zeroed per launch)
+    DevError* err;
+    long long wait_ns;           // bound of every device-side wait
+};
+
+template <typename Real>
+struct MonoParams {
+    const Real* cur;   // u^n (canonical) / u^n (increment)
+    Real* prev;        // canonical: u^{n-1} in, u^{n+1} out (in place); increment: v^n in/out
+    Real* unew;        // increment: u^{n+1} out; canonical: unused
+    const ProbeDev<Real>* probes;
+    int32_t nprobe;
+    int32_t form;
+    int64_t base;
+    int64_t nx;
+    int64_t n;         // level of `cur`
+    const Real* fA;
+    const Real* fB;
+    Real c2;
+    Real k;
+};
+
+struct VariantInfo {
+    int dtype;
+    int form;
+    int P;
+    int NT;
+};
+
+// span_kernel.cu
+int span_variant_count();
+VariantInfo span_variant_info(int v);
+size_t span_smem_bytes(int v);
+cudaError_t span_prepare(int v);  // sets the dynamic shared-memory attribute
+cudaError_t span_occupancy(int v, int* blocks_per_sm);
+cudaError_t span_launch(int v, const void* params, int grid, cudaStream_t s);
+
+// mono_kernel.cu
+cudaError_t mono_launch(int dtype, const void* params, cudaStream_t s);
+cudaError_t probe_final_launch(int dtype, const void* probes, int nprobe, const void* q0, int64_t level,
+                               cudaStream_t s);
+cudaError_t set_boundary_launch(int dtype, int form, void* q0, void* q1, const void* problems, int nprob,
+                                cudaStream_t s);
+
+}  // namespace rswr

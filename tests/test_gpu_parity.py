@@ -1,0 +1,322 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bar: bit-exact in both precisions when the oracle runs the same operation
+order (canonical FP64, increment FP32, and the other two combinations), and
+|err|/max|u| <= 1e-5 for FP32 against the FP64 oracle.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from paper_2203_10477_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CAN, INC = 1, 2          # library form codes
+ORACLE_FORM = {CAN: 0, INC: 1}
+F32, F64 = 0, 1
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_10477_gb300 import build, rswr
+
+    build.build()
+    return rswr
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def prec(dtype):
+    return "f64" if dtype == F64 else "f32"
+
+
+def assert_bitwise(a, b, what=""):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    assert a.shape == b.shape, (what, a.shape, b.shape)
+    bad = np.flatnonzero(a != b)
+    assert bad.size == 0, f"{what}: {bad.size} mismatches, first at {bad[:5]}: {a.ravel()[bad[:5]]} vs {b.ravel()[bad[:5]]}"
+
+
+# ----------------------------------------------------------------------------
+# config 1 (nx = 1001, N = 2, overlap 16, CFL 0.5, 2000 steps, FP64)
+# ----------------------------------------------------------------------------
+
+def test_c1_rswr_equals_oracle_bitwise(R, oracle_mod):
+    p = inputs.c1()
+    plan = R.Plan.from_problem(p, dtype=F64)
+    info = plan.info()
+    assert info["span_steps"] == 8
+    jr = 500
+    out = plan.run(p.fA, p.fB, p.T, traces=True, j_r=jr)
+    plan.check()
+    ref = oracle_mod.leapfrog(p.nx, p.T, p.a, p.dt, p.fA, p.fB, rec_j=[jr])
+    assert np.abs(ref["u"]).max() > 0.5
+    assert_bitwise(host(out["u"]), ref["u"], "u^T")
+    assert_bitwise(host(out["w"]), ref["w"], "u^{T-1}")
+    assert_bitwise(host(out["recv"]), ref["rec"][0], "receiver")
+    rs = oracle_mod.rswr_mask(p.nx, p.T, p.a, p.dt, p.fA, p.fB, p.n_sub, p.overlap)
+    assert_bitwise(host(out["traces"]), rs["traces"], "interface output waveforms")
+
+
+def test_c1_coefficients_match_oracle(R, oracle_mod):
+    p = inputs.c1()
+    info = R.Plan.from_problem(p, dtype=F64).info()
+    cf = oracle_mod.coeffs(p.xa, p.xb, p.a, p.nx, p.dt)
+    assert info["c2"] == cf.c2 and info["k"] == cf.k and info["inv2dx"] == cf.inv2dx
+    assert np.float32(info["c2f"]) == cf.c2f and np.float32(info["kf"]) == cf.kf
+
+
+def test_c1_monolithic_equals_oracle_bitwise(R, oracle_mod):
+    p = inputs.c1()
+    plan = R.Plan.from_problem(p, dtype=F64)
+    out = plan.mono(p.fA, p.fB, p.T, traces=True, j_r=123)
+    ref = oracle_mod.leapfrog(p.nx, p.T, p.a, p.dt, p.fA, p.fB, rec_j=[123])
+    assert_bitwise(host(out["u"]), ref["u"], "mono u")
+    assert_bitwise(host(out["w"]), ref["w"], "mono w")
+    assert_bitwise(host(out["recv"]), ref["rec"][0], "mono receiver")
+    rs = oracle_mod.rswr_mask(p.nx, p.T, p.a, p.dt, p.fA, p.fB, p.n_sub, p.overlap)
+    assert_bitwise(host(out["traces"]), rs["traces"], "mono traces")
+
+
+# ----------------------------------------------------------------------------
+# every dtype x form, several tilings, ragged tails, random initial data
+# ----------------------------------------------------------------------------
+
+CASES = [
+    # nx, N, ov, T, cfl
+    (1001, 2, 16, 300, 0.5),
+    (9973, 7, 24, 257, 0.9),     # prime nx: ragged last tile
+    (20000, 4, 64, 411, 0.9),    # several CTA tiles per subdomain
+    (4099, 3, 10, 96, 0.7),      # odd overlap half: S = 5
+    (517, 1, 8, 33, 1.0),        # one subdomain, Courant number exactly 1
+]
+
+
+@pytest.mark.parametrize("dtype,form", [(F64, CAN), (F64, INC), (F32, INC), (F32, CAN)])
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_random_state_bitwise(R, oracle_mod, dtype, form, case, mode):
+    nx, N, ov, T, cfl = case
+    dt = cfl / (nx - 1)
+    fA = inputs.ramped_sine(T, dt, freq=13.0)
+    fB = 0.5 * inputs.ramped_sine(T, dt, freq=7.0)
+    q0 = inputs.smooth_random_state(nx, seed=nx + T)
+    q1 = q0 * 0.999
+    if form == INC:
+        q1 = q0 - q1  # v^0 = u^0 - u^{-1}
+    plan = R.Plan(0.0, 1.0, 1.0, nx, dt, N, ov, dtype=dtype, form=form)
+    plan.set_mode(mode)
+    jr = nx // 3
+    out = plan.run(fA, fB, T, q0=q0, q1=q1, traces=N > 1, j_r=jr)
+    plan.check()
+    dt_ = np.float64 if dtype == F64 else np.float32
+    ref = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, fB, form=ORACLE_FORM[form], prec=prec(dtype),
+                              q0=q0.astype(dt_), q1=q1.astype(dt_), rec_j=[jr])
+    assert_bitwise(host(out["u"]), ref["u"], "u")
+    assert_bitwise(host(out["w"]), ref["w"], "w")
+    assert_bitwise(host(out["recv"]), ref["rec"][0], "receiver")
+    if N > 1:
+        rs = oracle_mod.rswr_mask(nx, T, 1.0, dt, fA, fB, N, ov, form=ORACLE_FORM[form], prec=prec(dtype),
+                                  q0=q0.astype(dt_), q1=q1.astype(dt_))
+        assert_bitwise(host(out["traces"]), rs["traces"], "traces")
+
+
+@pytest.mark.parametrize("dtype,form", [(F64, CAN), (F32, INC)])
+def test_every_variant_and_span_gives_identical_bits(R, oracle_mod, dtype, form):
+    nx, N, ov, T = 30011, 5, 48, 203
+    dt = 0.85 / (nx - 1)
+    fA = inputs.gaussian_pulse(T, dt, sigma_steps=15)
+    q0 = inputs.smooth_random_state(nx, seed=3)
+    dt_ = np.float64 if dtype == F64 else np.float32
+    ref = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, np.zeros(T + 1), form=ORACLE_FORM[form], prec=prec(dtype),
+                              q0=q0.astype(dt_))
+    plan = R.Plan(0.0, 1.0, 1.0, nx, dt, N, ov, dtype=dtype, form=form)
+    vs = [v for v in R.variants() if v["dtype"] == dtype and v["form"] == form]
+    assert len(vs) >= 2
+    for v in vs:
+        plan.set_variant(v["variant"])
+        for S in (1, 7, ov // 2):
+            plan.set_span(S)
+            for mode in (0, 1):
+                plan.set_mode(mode)
+                out = plan.run(fA, None, T, q0=q0)
+                plan.check()
+                assert_bitwise(host(out["u"]), ref["u"], f"variant {v} S={S} mode={mode}")
+                assert_bitwise(host(out["w"]), ref["w"], f"variant {v} S={S} mode={mode}")
+
+
+@pytest.mark.parametrize("T", [0, 1, 5, 31, 32, 33])
+def test_short_and_ragged_spans(R, oracle_mod, T):
+    nx, N, ov = 3001, 3, 64
+    dt = 0.9 / (nx - 1)
+    fA = inputs.ramped_sine(T, dt, freq=50.0) + 0.25
+    q0 = inputs.smooth_random_state(nx, seed=11)
+    plan = R.Plan(0.0, 1.0, 1.0, nx, dt, N, ov, dtype=F64)
+    out = plan.run(fA, None, T, q0=q0, traces=True, j_r=1500)
+    ref = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, np.zeros(T + 1), q0=q0, rec_j=[1500])
+    assert_bitwise(host(out["u"]), ref["u"], "u")
+    assert_bitwise(host(out["w"]), ref["w"], "w")
+    assert_bitwise(host(out["recv"]), ref["rec"][0], "receiver")
+
+
+def test_smallest_grids(R, oracle_mod):
+    for nx, N, ov in ((3, 1, 2), (4, 2, 2), (9, 2, 4), (64, 4, 16)):
+        T = 40
+        dt = 0.8 / (nx - 1)
+        fA = inputs.ramped_sine(T, dt, freq=3.0)
+        plan = R.Plan(0.0, 1.0, 1.0, nx, dt, N, ov, dtype=F64)
+        out = plan.run(fA, None, T)
+        ref = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, np.zeros(T + 1))
+        assert_bitwise(host(out["u"]), ref["u"], f"nx={nx}")
+
+
+def test_fp32_within_1e5_of_fp64_oracle(R, oracle_mod):
+    nx, N, ov, T = 60001, 8, 64, 5000
+    dt = 0.9 / (nx - 1)
+    fA = inputs.gaussian_pulse(T, dt)
+    plan = R.Plan(0.0, 1.0, 1.0, nx, dt, N, ov, dtype=F32)
+    out = plan.run(fA, None, T)
+    ref = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, np.zeros(T + 1), nx_run=oracle_mod.causal_extent(T, nx))
+    u = host(out["u"]).astype(np.float64)
+    n = len(ref["u"])
+    err = np.abs(u[:n] - ref["u"]).max() / np.abs(ref["u"]).max()
+    assert err <= 1e-5, err
+    assert np.all(u[n:] == 0.0)
+
+
+def test_run_host_matches_device_run(R):
+    p = inputs.c1()
+    plan = R.Plan.from_problem(p, dtype=F64)
+    dev = plan.run(p.fA, p.fB, p.T, traces=True, j_r=77)
+    hst = plan.run_host(p.fA, p.fB, p.T, traces=True, j_r=77)
+    assert_bitwise(hst["u"].numpy(), host(dev["u"]), "u")
+    assert_bitwise(hst["traces"].numpy(), host(dev["traces"]), "traces")
+    assert_bitwise(hst["recv"].numpy(), host(dev["recv"]), "recv")
+
+
+def test_rswr_equals_monolithic_gpu(R):
+    nx, N, ov, T = 100003, 16, 64, 700
+    dt = 0.9 / (nx - 1)
+    q0 = inputs.smooth_random_state(nx, seed=8)
+    fA = inputs.gaussian_pulse(T, dt, sigma_steps=10)
+    for dtype in (F64, F32):
+        plan = R.Plan(0.0, 1.0, 1.0, nx, dt, N, ov, dtype=dtype)
+        a = plan.run(fA, None, T, q0=q0, j_r=4)
+        b = plan.mono(fA, None, T, q0=q0, j_r=4)
+        assert_bitwise(host(a["u"]), host(b["u"]), "u")
+        assert_bitwise(host(a["w"]), host(b["w"]), "w")
+        assert_bitwise(host(a["recv"]), host(b["recv"]), "recv")
+
+
+# ----------------------------------------------------------------------------
+# batches of uneven problems
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", [F32, F64])
+def test_batch_each_problem_equals_its_oracle(R, oracle_mod, dtype):
+    r = inputs.rng(99)
+    P, T = 23, 300
+    probs = []
+    for i in range(P):
+        nx = int(r.integers(200, 40000))
+        a = float(r.uniform(0.5, 2.0))
+        dt = inputs.dt_for_cfl(nx, a, 0.8)
+        probs.append(inputs.Problem(nx, a, dt, T, max(1, -(-nx // 2048)), 32, inputs.sine(T, dt, float(r.uniform(1, 20))),
+                                    np.zeros(T + 1)))
+    b = R.Batch(probs, dtype=dtype)
+    fA = np.concatenate([p.fA for p in probs])
+    jr = np.array([p.nx // 2 for p in probs])
+    out = b.run(fA, None, T, j_r=jr)
+    b.check()
+    u = host(out["u"])
+    w = host(out["w"])
+    rec = host(out["recv"])
+    off = b.offsets
+    form = 0 if dtype == F64 else 1
+    for i, p in enumerate(probs):
+        ref = oracle_mod.leapfrog(p.nx, T, p.a, p.dt, p.fA, p.fB, form=form, prec=prec(dtype), rec_j=[p.nx // 2])
+        assert_bitwise(u[off[i]:off[i + 1]], ref["u"], f"problem {i} u")
+        assert_bitwise(w[off[i]:off[i + 1]], ref["w"], f"problem {i} w")
+        assert_bitwise(rec[i], ref["rec"][0], f"problem {i} receiver")
+
+
+# ----------------------------------------------------------------------------
+# adjoint: gradient w.r.t. the boundary waveform
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("jr", [1, 7, 150, 299, 0])
+def test_adjoint_grad_fA_fp64_bitwise(R, oracle_mod, jr):
+    nx, N, ov, T = 301, 3, 16, 420
+    a = 1.3
+    dt = 0.9 / (nx - 1) / a
+    g = inputs.lowpass_noise(T, seed=21)
+    z = np.zeros(T + 1)
+    w = inputs.rng(5).standard_normal(T + 1)
+    plan = R.Plan(0.0, 1.0, a, nx, dt, N, ov, dtype=F64)
+    res = plan.adjoint(g, None, T, jr, w)
+    ref = oracle_mod.adjoint(nx, T, a, dt, g, z, jr, w)
+    assert np.abs(ref["dg"]).max() > 0
+    assert_bitwise(host(res["grad_fA"]), ref["dg"], "grad_fA")
+
+
+def test_adjoint_grad_fA_fp32_close(R, oracle_mod):
+    nx, N, ov, T = 3001, 4, 64, 2000
+    a = 1.3
+    dt = 0.9 / (nx - 1) / a
+    g = inputs.lowpass_noise(T, seed=2)
+    w = inputs.rng(6).standard_normal(T + 1)
+    plan = R.Plan(0.0, 1.0, a, nx, dt, N, ov, dtype=F32)
+    res = plan.adjoint(g, None, T, 1200, w)
+    ref = oracle_mod.adjoint(nx, T, a, dt, g, np.zeros(T + 1), 1200, w)
+    got = host(res["grad_fA"]).astype(np.float64)
+    err = np.linalg.norm(got - ref["dg"]) / np.linalg.norm(ref["dg"])
+    assert err <= 1e-4, err
+
+
+def test_autograd_function_matches_oracle(R, oracle_mod):
+    nx, N, ov, T = 501, 2, 32, 300
+    a = 1.0
+    dt = 0.9 / (nx - 1)
+    g = torch.tensor(inputs.lowpass_noise(T, seed=4), dtype=torch.float64, device="cuda", requires_grad=True)
+    target = torch.zeros(T + 1, dtype=torch.float64, device="cuda")
+    plan = R.Plan(0.0, 1.0, a, nx, dt, N, ov, dtype=F64)
+    fn = R.rswr_function()
+    tr = fn.apply(g, plan, T, 200)
+    loss = ((tr - target) ** 2).sum()
+    loss.backward()
+    ref = oracle_mod.misfit_grad(nx, T, a, dt, host(g), np.zeros(T + 1), 200, np.zeros(T + 1))
+    assert abs(loss.item() - ref["loss"]) <= 1e-12 * ref["loss"]
+    np.testing.assert_allclose(host(g.grad), ref["dg"], rtol=1e-12, atol=1e-14 * np.abs(ref["dg"]).max())
+
+
+# ----------------------------------------------------------------------------
+# bounded waits: a tile that never publishes makes its neighbours time out
+# ----------------------------------------------------------------------------
+
+def test_missing_flag_times_out_and_context_survives(R, oracle_mod):
+    nx, N, ov, T = 50000, 4, 64, 400
+    dt = 0.9 / (nx - 1)
+    fA = inputs.gaussian_pulse(T, dt, sigma_steps=10)
+    plan = R.Plan(0.0, 1.0, 1.0, nx, dt, N, ov, dtype=F64)
+    assert plan.info()["ntiles"] >= 3
+    plan.set_mode(R.MODE_PERSISTENT)
+    plan.set_wait_limit(0.2)
+    plan.inject_missing_flag(1, 3)
+    plan.run(fA, None, T)
+    with pytest.raises(R.RSWRError) as ei:
+        plan.check()
+    assert ei.value.status == 6
+    # the context is still usable and a clean run is exact
+    plan.inject_missing_flag(-1, 0)
+    out = plan.run(fA, None, T)
+    plan.check()
+    ref = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, np.zeros(T + 1), nx_run=oracle_mod.causal_extent(T, nx))
+    assert_bitwise(host(out["u"])[: len(ref["u"])], ref["u"], "after timeout")
