@@ -1,0 +1,461 @@
+#!/usr/bin/env python3
+"""RSWR benchmark: GLUP/s of the RSWR hot path on one GB300 (or N replicas).
+
+Workload (one "step" = one whole RSWR run, every span of predict / select /
+update): 1-D wave u_tt = u_xx on [0, 1], nx = 2**24 points, N = 1024
+subdomains with a 64-point overlap (span S = 32), Courant number 0.9,
+10**4 time steps, left boundary a Gaussian pulse (sigma = 50 dt, t0 = 4 sigma),
+right boundary 0, zero initial data, interface output waveforms of all 1023
+interfaces recorded.  GLUP/s counts useful interior updates: (nx - 2) * T per
+step.
+
+The headline line is the FP64 run (canonical form, bit-identical to the FP64
+oracle); the same line carries the FP32 run (increment form), the monolithic
+GPU leapfrog comparators, the span kernel's roofline, the end-to-end number
+through the C ABI with host buffers, the CPU oracle baseline and the SM clocks
+seen during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own replica of the workload (the problem is
+not split across GPUs); the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2203_10477_gb300 import inputs  # noqa: E402
+
+METRIC = "GLUP/s and % stencil roofline, RSWR vs monolithic GPU leapfrog at FP64-matched error"
+UNIT = "GLUP/s"
+WORKLOAD = "1-D wave a=1, nx=2^24, N=1024 subdomains, overlap 64, CFL 0.9, 10^4 steps, Gaussian pulse"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+def load_peaks() -> dict:
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def alu_peaks(sm_mhz: float) -> dict:
+    """Arithmetic-pipe-bound LUP rates of the span kernel's fast path.
+
+    FP64 canonical form: 3 FP64-pipe instructions per update (DADD, 2 DFMA);
+    GB300 issues 2 FP64 instructions per clock per SM (its 1.25 TFLOP/s FP64
+    rating at 2.07 GHz on 152 SMs).  FP32 increment form: 4 FP32-pipe
+    instructions per update (3 FADD, 1 FFMA) at 128 lanes per clock per SM."""
+    f = sm_mhz * 1e6
+    return {"f64": SM_COUNT * 2 * f / 3 / 1e9, "f32": SM_COUNT * 128 * f / 4 / 1e9}
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for name, val in zip(names, r[2][1:]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# the reference arm and the CPU baseline: the oracle on the host cores
+# ----------------------------------------------------------------------------
+
+def oracle_sample(p, steps: int) -> float:
+    """Seconds for `steps` leapfrog steps of the CPU oracle over the full grid."""
+    import oracle
+
+    t0 = time.perf_counter()
+    oracle.leapfrog(p.nx, steps, p.a, p.dt, p.fA[: steps + 1], p.fB[: steps + 1])
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(p, budget_s: float = 15.0) -> dict:
+    import oracle
+
+    oracle.build()
+    t1 = oracle_sample(p, 2)
+    steps = int(max(2, min(p.T, budget_s / max(t1 / 2, 1e-9))))
+    secs = oracle_sample(p, steps)
+    lups = (p.nx - 2) * steps
+    return {"value": lups / secs / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 canonical oracle leapfrog (plain C, one thread), full nx=2^24 grid, {steps} of the "
+                      f"10^4 steps, {secs:.1f} s"}
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    if rank != 0:
+        return
+    p = inputs.c2()
+    import oracle
+
+    oracle.build()
+    t1 = oracle_sample(p, 2)
+    steps_per = int(max(2, min(p.T, 4.0 / max(t1 / 2, 1e-9))))  # about 4 s of CPU work per step
+    for _ in range(args.warmup):
+        oracle_sample(p, steps_per)
+    times = [oracle_sample(p, steps_per) for _ in range(args.steps)]
+    total = sum(times)
+    lups = (p.nx - 2) * steps_per * args.steps
+    value = lups / total / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "nx": p.nx, "n_sub": p.n_sub, "overlap": p.overlap, "cfl": 0.9,
+                   "T": p.T, "sample_steps_per_step": steps_per},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step: FP64 oracle leapfrog over the full nx=2^24 grid for {steps_per} "
+                                   f"of the 10^4 time steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def gpu_uuid(torch, dev) -> str:
+    try:
+        u = torch.cuda.get_device_properties(dev).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        return str(dev.index or 0)
+
+
+class RunBench:
+    """Device buffers and timing events for repeated whole RSWR runs of one plan."""
+
+    def __init__(self, torch, plan, p):
+        from paper_2203_10477_gb300 import rswr
+
+        self.torch, self.plan, self.p = torch, plan, p
+        td = torch.float64 if plan.dtype == rswr.F64 else torch.float32
+        self.fA = torch.as_tensor(p.fA, device="cuda").to(td)
+        self.fB = torch.as_tensor(p.fB, device="cuda").to(td)
+        self.out = (torch.empty(p.nx, dtype=td, device="cuda"), torch.empty(p.nx, dtype=td, device="cuda"))
+        self.k0 = torch.cuda.Event(enable_timing=True)
+        self.k1 = torch.cuda.Event(enable_timing=True)
+        # torch creates the CUDA events on first record: create them before the
+        # library is given their handles
+        self.k0.record()
+        self.k1.record()
+        torch.cuda.synchronize()
+
+    def warmup(self, n):
+        for _ in range(n):
+            self.plan.run(self.fA, self.fB, self.p.T, traces=True, out=self.out)
+        self.torch.cuda.synchronize()
+        self.plan.check()
+
+    def timed(self, steps, flush):
+        """Per-step (whole run ms, span-kernel ms), each on the launching stream."""
+        torch = self.torch
+        stream = torch.cuda.current_stream()
+        self.plan.set_kernel_events(self.k0, self.k1)
+        run_ms, ker_ms = [], []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            self.plan.run(self.fA, self.fB, self.p.T, traces=True, out=self.out)
+            e1.record(stream)
+            e1.synchronize()
+            run_ms.append(e0.elapsed_time(e1))
+            ker_ms.append(self.k0.elapsed_time(self.k1))
+        self.plan.set_kernel_events(None, None)
+        self.plan.check()
+        return run_ms, ker_ms
+
+
+def mono_runs(torch, plan, p, steps, flush):
+    stream = torch.cuda.current_stream()
+    from paper_2203_10477_gb300 import rswr
+
+    fA = torch.as_tensor(p.fA, device="cuda").to(torch.float64 if plan.dtype == rswr.F64 else torch.float32)
+    out = (torch.empty(p.nx, dtype=fA.dtype, device="cuda"), torch.empty(p.nx, dtype=fA.dtype, device="cuda"))
+    plan.mono(fA, None, p.T, out=out)  # warm-up
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.mono(fA, None, p.T, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms
+
+
+def e2e_run(torch, plan, p, steps):
+    """rswr_run_host: pinned host waveforms in, final state pair + traces out."""
+    from paper_2203_10477_gb300 import rswr
+
+    td = torch.float64 if plan.dtype == rswr.F64 else torch.float32
+    es = 8 if plan.dtype == rswr.F64 else 4
+    fA = torch.as_tensor(p.fA).to(td).pin_memory()
+    fB = torch.as_tensor(p.fB).to(td).pin_memory()
+    out = (torch.empty(p.nx, dtype=td).pin_memory(), torch.empty(p.nx, dtype=td).pin_memory())
+    plan.run_host(fA, fB, p.T, out=out)  # warm-up
+    stream = torch.cuda.current_stream()
+    ms = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.run_host(fA, fB, p.T, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    h2d = 2 * (p.T + 1) * es
+    d2h = 2 * p.nx * es
+    return ms, h2d, d2h
+
+
+def profile_case(which: str) -> None:
+    """The workload of the bench at nx = 2^22 and 320 steps (10 spans): state
+    arrays of 32 MiB (FP64) / 16 MiB (FP32) each, four of them, so DRAM counters
+    still see traffic beyond L2, and one span-kernel launch of a few ms."""
+    import torch
+
+    from paper_2203_10477_gb300 import build, rswr
+
+    build.build()
+    p = inputs.c2(T=320, nx=1 << 22)
+    plan = rswr.Plan.from_problem(p, dtype=rswr.F64 if which == "f64" else rswr.F32)
+    for _ in range(2):
+        plan.run(p.fA, p.fB, p.T, traces=True)
+    torch.cuda.synchronize()
+    plan.check()
+    print(json.dumps({"profile_case": which, "nx": p.nx, "T": p.T, "info": plan.info()}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mono", action="store_true")
+    ap.add_argument("--profile-case", choices=["f64", "f32"], default=None,
+                    help="run the small profiling case (nx=2^22, 320 steps) twice and exit (for ncu)")
+    args = ap.parse_args()
+
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+
+        dist_.init_process_group("nccl", device_id=dev)
+        dist = dist_
+
+    from paper_2203_10477_gb300 import build, rswr
+
+    build.build()
+    p = inputs.c2()
+    lups = (p.nx - 2) * p.T
+    peaks = load_peaks()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MiB > 129 MB L2
+
+    plan64 = rswr.Plan.from_problem(p, dtype=rswr.F64, device=dev)
+    plan32 = rswr.Plan.from_problem(p, dtype=rswr.F32, device=dev)
+    v64 = plan64.autotune(3 * 32)
+    v32 = plan32.autotune(3 * 32)
+    info64, info32 = plan64.info(), plan32.info()
+
+    b64, b32 = RunBench(torch, plan64, p), RunBench(torch, plan32, p)
+    b64.warmup(args.warmup)
+    b32.warmup(args.warmup)
+
+    clocks = ClockSampler(gpu_uuid(torch, dev))
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    run64, ker64 = b64.timed(args.steps, flush)
+    run32, ker32 = b32.timed(args.steps, flush)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+
+    t64 = sum(run64) / 1e3
+    t32 = sum(run32) / 1e3
+    if dist:
+        tt = torch.tensor([t64, t32], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t64, t32 = tt.tolist()
+    n = world
+    value64 = n * lups * args.steps / t64 / 1e9
+    value32 = n * lups * args.steps / t32 / 1e9
+
+    mono = {}
+    if not args.no_mono:
+        for name, dtype in (("f64", rswr.F64), ("f32", rswr.F32)):
+            pl = plan64 if dtype == rswr.F64 else plan32
+            ms = mono_runs(torch, pl, p, 1, flush)
+            mono[name] = {"value": lups / (sum(ms) / 1e3) / 1e9, "unit": UNIT, "ms_per_step": sum(ms) / len(ms),
+                          "form": "canonical" if dtype == rswr.F64 else "increment"}
+
+    e2e_ms, h2d, d2h = e2e_run(torch, plan64, p, max(1, min(args.steps, 3)))
+    e2e_value = lups / (sum(e2e_ms) / len(e2e_ms) / 1e3) / 1e9
+
+    sm_mhz = clk["sm_mhz"] if clk else SM_MAX_MHZ
+    alu_max = alu_peaks(SM_MAX_MHZ)
+    alu_run = alu_peaks(sm_mhz)
+    r_hbm = {"f64": peaks["hbm_gbs"] / 24.0, "f32": peaks["hbm_gbs"] / 12.0}
+
+    # span kernel (the dominant kernel): achieved LUP rate over its own launches
+    k64 = lups / (statistics.mean(ker64) / 1e3) / 1e9
+    k32 = lups / (statistics.mean(ker32) / 1e3) / 1e9
+    # algorithmic bytes per LUP of RSWR with the subdomain geometry:
+    # w * (2 (core + ov) + 2 core) / (core * S), core = nx / N
+    core_sub = p.nx / p.n_sub
+    bpl = lambda w: w * (2 * (core_sub + p.overlap) + 2 * core_sub) / (core_sub * info64["span_steps"])
+
+    line = {
+        "metric": METRIC,
+        "value": value64,
+        "unit": UNIT,
+        "n_gpus": n,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * t64 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": p.nx, "n_sub": p.n_sub, "overlap": p.overlap, "cfl": 0.9,
+                   "T": p.T, "span_steps": info64["span_steps"], "lups_per_step": lups,
+                   "traces": "all 1023 interfaces x 2 output waveforms per level",
+                   "l2": "flushed between steps (256 MiB write); state > L2",
+                   "variant_f64": {k: info64[k] for k in ("variant", "points_per_thread", "threads_per_cta",
+                                                            "window", "core", "mode")},
+                   "variant_f32": {k: info32[k] for k in ("variant", "points_per_thread", "threads_per_cta",
+                                                            "window", "core", "mode")},
+                   "replicas": "one independent replica per GPU" if n > 1 else None},
+        "pct_stencil_roofline": 100.0 * value64 / n / r_hbm["f64"],
+        "stencil_roofline": {"f64_glups": r_hbm["f64"], "f32_glups": r_hbm["f32"],
+                             "definition": "HBM-bound untiled leapfrog: measured copy GB/s / (3 w) bytes per LUP",
+                             "hbm_gbs": peaks["hbm_gbs"], "source": peaks["source"]},
+        "roofline": {"bound": "alu", "kernel": "span_kernel<double, canonical>",
+                     "achieved": k64, "peak": alu_max["f64"], "unit": "GLUP/s",
+                     "frac": k64 / alu_max["f64"], "frac_at_run_clock": k64 / alu_run["f64"],
+                     "traffic": None,
+                     "algorithmic_bytes_per_lup": bpl(8),
+                     "achieved_gbs": k64 * bpl(8),
+                     "peak_definition": "152 SMs x 2 FP64 instr/clk x 2070 MHz / 3 FP64 instr per LUP"},
+        "f32": {"value": value32, "unit": UNIT, "ms_per_step": 1e3 * t32 / args.steps, "form": "increment",
+                "pct_stencil_roofline": 100.0 * value32 / n / r_hbm["f32"],
+                "error_vs_fp64_oracle": "<= 1e-5 relative (tests/test_gpu_parity.py)",
+                "roofline": {"bound": "alu", "kernel": "span_kernel<float, increment>", "achieved": k32,
+                             "peak": alu_max["f32"], "unit": "GLUP/s", "frac": k32 / alu_max["f32"],
+                             "frac_at_run_clock": k32 / alu_run["f32"], "traffic": None,
+                             "algorithmic_bytes_per_lup": bpl(4), "achieved_gbs": k32 * bpl(4),
+                             "peak_definition": "152 SMs x 128 FP32 lanes x 2070 MHz / 4 FP32 instr per LUP"}},
+        "monolithic": mono,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "path": "rswr_run_host (C ABI, pinned host buffers, copies inside the timed region)"},
+        "gpu_launches": 3 * 2 * args.steps,
+        "gpu_launches_detail": "per timed run: set_boundary_kernel + span_kernel (persistent: one launch for all "
+                               "313 spans) + probe_final_kernel; FP64 and FP32 runs",
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -141,6 +141,12 @@ rswr_status rswr_plan_set_wait_limit(rswr_plan_t plan, double seconds);
  * expire and the run reports RSWR_ETIMEOUT.  tile = -1 disables. */
 rswr_status rswr_plan_inject_missing_flag(rswr_plan_t plan, int32_t tile, int32_t span);
 
+/* Timing hook: when set, every run records `start` (a cudaEvent_t passed as
+ * void*) on its stream right before its first span (or step) kernel and
+ * `stop` right after its last one, so a caller can time the kernels alone.
+ * NULL, NULL clears the hook.  The events stay owned by the caller. */
+rswr_status rswr_plan_set_kernel_events(rswr_plan_t plan, void* start, void* stop);
+
 /* Times every kernel variant of the plan's dtype/form (and both modes) on
  * `probe_steps` steps of a zero-data run and keeps the fastest; returns its
  * index in *variant (may be NULL).  Uses the plan's workspace; synchronous. */
@@ -228,6 +234,7 @@ rswr_status rswr_batch_get_info(rswr_batch_t batch, rswr_plan_info* info);
 rswr_status rswr_batch_set_mode(rswr_batch_t batch, int32_t mode);
 rswr_status rswr_batch_set_variant(rswr_batch_t batch, int32_t variant);
 rswr_status rswr_batch_set_wait_limit(rswr_batch_t batch, double seconds);
+rswr_status rswr_batch_set_kernel_events(rswr_batch_t batch, void* start, void* stop);
 rswr_status rswr_batch_check(rswr_batch_t batch, void* stream, int32_t* code, int32_t* tile, int32_t* span);
 
 /* All problems advance T steps in one persistent launch (default mode).

@@ -109,6 +109,8 @@ struct Engine {
     size_t host_stage_cap = 0;
     void* d_scratch[2] = {nullptr, nullptr};  // adjoint scratch outputs
     size_t scratch_cap = 0;
+    cudaEvent_t ev_start = nullptr;  // caller-owned timing events (rswr_*_set_kernel_events)
+    cudaEvent_t ev_stop = nullptr;
 
     size_t esize() const { return dtype == kF64 ? 8 : 4; }
 };
@@ -512,6 +514,7 @@ rswr_status run_impl(Engine* e, const RunReq& r, cudaStream_t s)
 
     const void* fin0;
     const void* fin1;
+    if (e->ev_start) RSWR_CUDA(cudaEventRecord(e->ev_start, s));
     if (!r.mono) {
         const int nspans = (int)((r.T + e->S - 1) / e->S);
         SpanParams<Real> prm = span_params<Real>(e, r.T, nspans);
@@ -575,6 +578,7 @@ rswr_status run_impl(Engine* e, const RunReq& r, cudaStream_t s)
             fin1 = b;
         }
     }
+    if (e->ev_stop) RSWR_CUDA(cudaEventRecord(e->ev_stop, s));
     RSWR_CUDA(probe_final_launch(e->dtype, e->d_probes, nprobe, fin0, r.T, s));
     if (r.out0 && (st = pack<Real>(e, r.out0, fin0, s)) != RSWR_OK) return st;
     if (r.out1 && (st = pack<Real>(e, r.out1, fin1, s)) != RSWR_OK) return st;
@@ -847,6 +851,15 @@ rswr_status rswr_plan_inject_missing_flag(rswr_plan_t plan, int32_t tile, int32_
     return RSWR_OK;
 }
 
+rswr_status rswr_plan_set_kernel_events(rswr_plan_t plan, void* start, void* stop)
+{
+    if (!plan) return fail(RSWR_EINVAL, "NULL plan");
+    if ((start == nullptr) != (stop == nullptr)) return fail(RSWR_EINVAL, "give both events or neither");
+    plan->e->ev_start = static_cast<cudaEvent_t>(start);
+    plan->e->ev_stop = static_cast<cudaEvent_t>(stop);
+    return RSWR_OK;
+}
+
 rswr_status rswr_plan_check(rswr_plan_t plan, void* stream, int32_t* code, int32_t* tile, int32_t* span)
 {
     if (!plan) return fail(RSWR_EINVAL, "NULL plan");
@@ -988,6 +1001,15 @@ rswr_status rswr_batch_set_wait_limit(rswr_batch_t batch, double seconds)
     if (!batch) return fail(RSWR_EINVAL, "NULL batch");
     if (!(seconds > 0.0) || seconds > 3600.0) return fail(RSWR_EINVAL, "wait limit out of range");
     batch->e->wait_s = seconds;
+    return RSWR_OK;
+}
+
+rswr_status rswr_batch_set_kernel_events(rswr_batch_t batch, void* start, void* stop)
+{
+    if (!batch) return fail(RSWR_EINVAL, "NULL batch");
+    if ((start == nullptr) != (stop == nullptr)) return fail(RSWR_EINVAL, "give both events or neither");
+    batch->e->ev_start = static_cast<cudaEvent_t>(start);
+    batch->e->ev_stop = static_cast<cudaEvent_t>(stop);
     return RSWR_OK;
 }
 

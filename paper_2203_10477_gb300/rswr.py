@@ -75,6 +75,8 @@ SIGNATURES = {
     "rswr_plan_set_wait_limit": (_st, [_vp, _dbl]),
     "rswr_plan_inject_missing_flag": (_st, [_vp, _i32, _i32]),
     "rswr_plan_autotune": (_st, [_vp, _i64, ctypes.POINTER(_i32), _vp]),
+    "rswr_plan_set_kernel_events": (_st, [_vp, _vp, _vp]),
+    "rswr_batch_set_kernel_events": (_st, [_vp, _vp, _vp]),
     "rswr_plan_check": (_st, [_vp, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "rswr_run": (_st, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "rswr_run_host": (_st, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
@@ -217,6 +219,13 @@ class Plan:
     def inject_missing_flag(self, tile: int, span: int):
         check(lib().rswr_plan_inject_missing_flag(self.h, tile, span))
 
+    def set_kernel_events(self, start=None, stop=None):
+        """torch.cuda.Event pair recorded around the kernels of every run (None clears)."""
+        h = lambda ev: None if ev is None else ev.cuda_event
+        if start is not None and (not h(start) or not h(stop)):
+            raise ValueError("record the events once before handing them over (torch creates them lazily)")
+        check(lib().rswr_plan_set_kernel_events(self.h, h(start), h(stop)))
+
     def autotune(self, probe_steps: int, stream=None) -> int:
         v = _i32()
         check(lib().rswr_plan_autotune(self.h, probe_steps, ctypes.byref(v), _stream(stream)))
@@ -336,6 +345,10 @@ class Batch:
 
     def set_wait_limit(self, seconds: float):
         check(lib().rswr_batch_set_wait_limit(self.h, seconds))
+
+    def set_kernel_events(self, start=None, stop=None):
+        h = lambda ev: None if ev is None else ev.cuda_event
+        check(lib().rswr_batch_set_kernel_events(self.h, h(start), h(stop)))
 
     def check(self, stream=None):
         c, t, s = _i32(), _i32(), _i32()
