@@ -254,6 +254,36 @@ rswr_status rswr_batch_adjoint(rswr_batch_t batch, const void* fA, const void* f
                                const void* wbar, void* grad_fA, double* grad_a, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Running without any allocation                                            */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The paper has no counterpart of this call; it exists for callers that may
+ * not allocate device memory where they solve -- for instance code running
+ * under a framework whose caching allocator already holds the memory the
+ * process may use, or latency-critical loops in which cudaMalloc/cudaFree,
+ * which synchronise the device, are not acceptable.
+ *
+ * Same problem, decomposition and results as rswr_plan_create + rswr_run
+ * (default form, no traces or receiver), but no plan: the call allocates
+ * nothing and works in a 32 MiB scratch area compiled into the library (every
+ * GPU that loads it keeps it until the process exits).  It needs
+ * 4 * (nx + about 2 CTA windows) * sizeof(element) bytes plus small tables:
+ * about nx <= 1.0e6 for RSWR_F64 and nx <= 2.0e6 for RSWR_F32; larger
+ * problems are rejected with RSWR_EINVAL and a message.
+ *   fA, fB   device, T+1 Dirichlet samples each, or NULL (zero)
+ *   q0, q1   device initial state pair or NULL (zero data / at rest)
+ *   out0, out1  device final state pair (required)
+ * The first call on each device looks up the scratch area's device address
+ * (with that device current); make that first call before any stream
+ * capture.  All calls share the scratch area and each clears what must start
+ * at zero; calls whose work overlaps on the GPU race and give wrong results.
+ */
+rswr_status rswr_run_noalloc(double xa, double xb, double a, int64_t nx, double dt, int32_t n_sub, int32_t overlap,
+                             int32_t dtype, const void* fA, const void* fB, int64_t T, const void* q0,
+                             const void* q1, void* out0, void* out1, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Kernel variants                                                           */
 /* ------------------------------------------------------------------------ */
 

@@ -741,6 +741,8 @@ rswr_status adjoint_g(Engine* e, int64_t T, const int64_t* j_r, const void* wbar
 
 }  // namespace
 
+void rswr::set_error_message(const char* m) { g_msg = m; }
+
 // ===========================================================================
 // C ABI
 // ===========================================================================

@@ -105,6 +105,9 @@ cudaError_t span_prepare(int v);  // sets the dynamic shared-memory attribute
 cudaError_t span_occupancy(int v, int* blocks_per_sm);
 cudaError_t span_launch(int v, const void* params, int grid, cudaStream_t s);
 
+// rswr_api.cu: sets the message returned by rswr_last_error_message()
+void set_error_message(const char* m);
+
 // mono_kernel.cu
 cudaError_t mono_launch(int dtype, const void* params, cudaStream_t s);
 cudaError_t probe_final_launch(int dtype, const void* probes, int nprobe, const void* q0, int64_t level,
