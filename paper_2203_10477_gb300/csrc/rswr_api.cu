@@ -111,6 +111,9 @@ struct Engine {
     size_t scratch_cap = 0;
     cudaEvent_t ev_start = nullptr;  // caller-owned timing events (rswr_*_set_kernel_events)
     cudaEvent_t ev_stop = nullptr;
+    // adjoint workspace (rswr_adjoint with dL/da): states, tables, partial sums
+    void* adj_mem = nullptr;
+    size_t adj_mem_cap = 0;
 
     size_t esize() const { return dtype == kF64 ? 8 : 4; }
 };
@@ -132,6 +135,7 @@ void free_engine(Engine* e)
     cudaFree(e->d_done);
     cudaFree(e->d_err);
     cudaFree(e->d_host_stage);
+    cudaFree(e->adj_mem);
     delete e;
 }
 
@@ -741,6 +745,276 @@ rswr_status adjoint_g(Engine* e, int64_t T, const int64_t* j_r, const void* wbar
 
 }  // namespace
 
+namespace {
+
+// Gradients of <wbar, receiver trace> w.r.t. fA and a with the forward levels
+// recomputed from checkpoints (see adjoint_kernel.cu for the kernel side).
+//   spans of SA steps (SA <= the adjoint variant's shared-memory store and <= S);
+//   checkpoints every C = ceil(sqrt(#spans)) spans during one forward sweep;
+//   per segment of C spans, last first: the span kernel recomputes the state at
+//   the start of every span of the segment, then the adjoint kernel runs the
+//   segment's spans last first (reversed-time adjoint levels ascending).
+template <typename Real>
+rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* fA, const void* fB, const void* wbar,
+                         void* grad, double* grad_a, cudaStream_t s)
+{
+    const int np = (int)e->probs.size();
+    const size_t es = sizeof(Real);
+    int va = -1;
+    for (int v = 0; v < adj_variant_count(); ++v) {
+        const VariantInfo vi = adj_variant_info(v);
+        if (vi.dtype == e->dtype && vi.form == e->form) {
+            va = v;
+            break;
+        }
+    }
+    if (va < 0) return fail(RSWR_ENOTSUP, "no adjoint kernel for this dtype/form");
+    const VariantInfo ai = adj_variant_info(va);
+    const int SA = std::min(e->S, adj_variant_span(va));
+    const int H = (SA + 3) / 4 * 4;
+    const int vf = e->variant;
+    const VariantInfo fi = span_variant_info(vf);
+    const int core_f = fi.P * fi.NT - 2 * H;
+    const int core_a = ai.P * ai.NT - 2 * H;
+    if (core_f < H || core_a < H) return fail(RSWR_EINVAL, "adjoint tiling: window too small");
+    const int64_t pad = H + 8;
+
+    // layout shared by the forward tiling (core_f) and the adjoint tiling (core_a)
+    std::vector<int64_t> base(np), t0f(np), tcf(np), t0a(np), tca(np);
+    int64_t at = 0, ntf = 0, nta = 0;
+    for (int p = 0; p < np; ++p) {
+        const int64_t nx = e->probs[p].nx;
+        tcf[p] = (nx + core_f - 1) / core_f;
+        tca[p] = (nx + core_a - 1) / core_a;
+        t0f[p] = ntf;
+        t0a[p] = nta;
+        ntf += tcf[p];
+        nta += tca[p];
+        base[p] = at + pad;
+        int64_t len = pad + std::max(tcf[p] * core_f, tca[p] * core_a) + pad;
+        at += (len + kAlign - 1) / kAlign * kAlign;
+    }
+    const int64_t slen = at;
+    const int64_t nspans = (T + SA - 1) / SA;
+    const int64_t C = std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)std::max<int64_t>(nspans, 1))));
+    const int64_t nck = std::max<int64_t>(1, (nspans + C - 1) / C);
+    const int64_t nstates = nck + C + 4;  // checkpoints | segment | forward work pair | adjoint pair
+
+    // one device block: states, partial sums, tables
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t arr = up(es * slen);
+    const size_t b_states = 2 * arr * nstates;
+    const size_t b_partial = up(sizeof(double) * std::max<int64_t>(nspans, 1) * nta);
+    const size_t b_tiles = up(sizeof(TileDev) * (ntf + nta));
+    const size_t b_prob = up(sizeof(ProblemDev<Real>) * 2 * np);
+    const size_t b_probes = up(sizeof(ProbeDev<Real>) * np);
+    const size_t b_red = up(sizeof(int64_t) * 2 * np + sizeof(double) * np);
+    const size_t need = b_states + b_partial + b_tiles + b_prob + b_probes + b_red;
+    if (need > e->adj_mem_cap) {
+        RSWR_CUDA(cudaStreamSynchronize(s));
+        cudaFree(e->adj_mem);
+        e->adj_mem = nullptr;
+        e->adj_mem_cap = 0;
+        if (cudaMalloc(&e->adj_mem, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(RSWR_ENOMEM, "adjoint workspace (" + std::to_string(need) + " bytes)");
+        }
+        e->adj_mem_cap = need;
+    }
+    char* mem = static_cast<char*>(e->adj_mem);
+    auto state0 = [&](int64_t i) { return reinterpret_cast<Real*>(mem + (2 * i) * arr); };
+    auto state1 = [&](int64_t i) { return reinterpret_cast<Real*>(mem + (2 * i + 1) * arr); };
+    char* q = mem + b_states;
+    double* partial = reinterpret_cast<double*>(q);
+    q += b_partial;
+    TileDev* d_tiles_f = reinterpret_cast<TileDev*>(q);
+    TileDev* d_tiles_a = d_tiles_f + ntf;
+    q += b_tiles;
+    ProblemDev<Real>* d_pu = reinterpret_cast<ProblemDev<Real>*>(q);
+    ProblemDev<Real>* d_pl = d_pu + np;
+    q += b_prob;
+    ProbeDev<Real>* d_probes = reinterpret_cast<ProbeDev<Real>*>(q);
+    q += b_probes;
+    int64_t* d_t0 = reinterpret_cast<int64_t*>(q);
+    int64_t* d_tc = d_t0 + np;
+    double* d_scale = reinterpret_cast<double*>(d_tc + np);
+    const int64_t CK0 = 0, SG0 = nck, WK0 = nck + C, LM0 = nck + C + 2;
+
+    // host tables
+    std::vector<TileDev> ht;
+    ht.reserve(ntf + nta);
+    for (int p = 0; p < np; ++p)
+        for (int64_t t = 0; t < tcf[p]; ++t) ht.push_back(TileDev{p, (int32_t)t, 0, 0});
+    std::vector<ProbeDev<Real>> hp;
+    std::vector<ProblemDev<Real>> hpr(2 * np);
+    std::vector<double> hscale(np);
+    for (int p = 0; p < np; ++p) {
+        const ProbHost& ph = e->probs[p];
+        const bool interior = j_r[p] > 0 && j_r[p] < ph.nx - 1;
+        for (int64_t t = 0; t < tca[p]; ++t) {
+            TileDev td{p, (int32_t)t, (int32_t)hp.size(), (int32_t)hp.size()};
+            if (t == 0 && interior) td.probe_end += 1;  // grid point 1 lies in the first core
+            ht.push_back(td);
+            if (t == 0 && interior) {
+                ProbeDev<Real> pr{};
+                pr.gidx = base[p] + 1;
+                pr.out = static_cast<Real*>(grad) + (int64_t)p * (T + 1) + T;
+                pr.stride = -1;
+                pr.nmax = T;
+                pr.scale = sizeof(Real) == 8 ? (Real)ph.c2 : (Real)ph.c2f;
+                pr.kind = 0;
+                hp.push_back(pr);
+            }
+        }
+        const Real c2 = sizeof(Real) == 8 ? (Real)ph.c2 : (Real)ph.c2f;
+        const Real k = sizeof(Real) == 8 ? (Real)ph.k : (Real)ph.kf;
+        ProblemDev<Real>& u = hpr[p];
+        u = ProblemDev<Real>{};
+        u.base = base[p];
+        u.nx = ph.nx;
+        u.tile0 = t0f[p];
+        u.ntiles = tcf[p];
+        u.fA = fA ? static_cast<const Real*>(fA) + (int64_t)p * (T + 1) : nullptr;
+        u.fB = fB ? static_cast<const Real*>(fB) + (int64_t)p * (T + 1) : nullptr;
+        u.js = -1;
+        u.c2 = c2;
+        u.k = k;
+        ProblemDev<Real>& l = hpr[np + p];
+        l = u;
+        l.tile0 = t0a[p];
+        l.ntiles = tca[p];
+        l.fA = nullptr;
+        l.fB = nullptr;
+        l.js = interior ? j_r[p] : -1;
+        l.src = static_cast<const Real*>(wbar) + (int64_t)p * (T + 1) + T + 1;
+        l.src_stride = -1;
+        hscale[p] = 2.0 * ph.c2 / ph.a;
+    }
+    // tile-local probe indices were assigned in adjoint-tile order; shift the
+    // forward tiles' empty ranges are already (0, 0)
+    RSWR_CUDA(cudaMemcpyAsync(d_tiles_f, ht.data(), sizeof(TileDev) * ht.size(), cudaMemcpyHostToDevice, s));
+    RSWR_CUDA(cudaMemcpyAsync(d_pu, hpr.data(), sizeof(ProblemDev<Real>) * hpr.size(), cudaMemcpyHostToDevice, s));
+    if (!hp.empty())
+        RSWR_CUDA(cudaMemcpyAsync(d_probes, hp.data(), sizeof(ProbeDev<Real>) * hp.size(), cudaMemcpyHostToDevice, s));
+    std::vector<int64_t> hred(2 * np);
+    for (int p = 0; p < np; ++p) {
+        hred[p] = t0a[p];
+        hred[np + p] = tca[p];
+    }
+    RSWR_CUDA(cudaMemcpyAsync(d_t0, hred.data(), sizeof(int64_t) * 2 * np, cudaMemcpyHostToDevice, s));
+    RSWR_CUDA(cudaMemcpyAsync(d_scale, hscale.data(), sizeof(double) * np, cudaMemcpyHostToDevice, s));
+    RSWR_CUDA(cudaMemsetAsync(e->d_err, 0, sizeof(DevError), s));
+
+    // dL/dfA: zero, or wbar itself for a receiver on the left Dirichlet node
+    RSWR_CUDA(cudaMemsetAsync(grad, 0, es * (T + 1) * np, s));
+    for (int p = 0; p < np; ++p)
+        if (j_r[p] == 0)
+            RSWR_CUDA(cudaMemcpyAsync(static_cast<char*>(grad) + es * (T + 1) * p,
+                                      static_cast<const char*>(wbar) + es * (T + 1) * p, es * (T + 1),
+                                      cudaMemcpyDeviceToDevice, s));
+    RSWR_CUDA(cudaMemsetAsync(partial, 0, b_partial, s));
+
+    int bps_f = 0, bps_a = 0;
+    RSWR_CUDA(span_occupancy(vf, &bps_f));
+    RSWR_CUDA(adj_occupancy(va, &bps_a));
+    const int grid_f = (int)std::min<int64_t>((int64_t)std::max(bps_f, 1) * e->num_sms, ntf);
+    const int grid_a = (int)std::min<int64_t>((int64_t)std::max(bps_a, 1) * e->num_sms, nta);
+
+    SpanParams<Real> fp{};
+    fp.problems = d_pu;
+    fp.tiles = d_tiles_f;
+    fp.probes = nullptr;
+    fp.ntiles = ntf;
+    fp.T = T;
+    fp.H = H;
+    fp.core = core_f;
+    fp.S = SA;
+    fp.nspans = (int32_t)nspans;
+    fp.inject_tile = -1;
+    fp.inject_span = -1;
+    fp.err = e->d_err;
+    fp.wait_ns = (long long)(e->wait_s * 1e9);
+    auto forward_span = [&](int64_t k, Real* s0, Real* s1, Real* d0, Real* d1) -> rswr_status {
+        fp.span = (int32_t)k;
+        fp.q0[k & 1] = s0;
+        fp.q1[k & 1] = s1;
+        fp.q0[(k + 1) & 1] = d0;
+        fp.q1[(k + 1) & 1] = d1;
+        RSWR_CUDA(span_launch(vf, &fp, grid_f, s));
+        return RSWR_OK;
+    };
+
+    // forward sweep with checkpoints
+    RSWR_CUDA(cudaMemsetAsync(state0(CK0), 0, 2 * arr, s));
+    RSWR_CUDA(set_boundary_launch(e->dtype, e->form, state0(CK0), state1(CK0), d_pu, np, s));
+    const int64_t last_ck_span = (nck - 1) * C;
+    for (int64_t k = 0; k < last_ck_span; ++k) {
+        const int64_t si = (k % C == 0) ? CK0 + k / C : WK0 + (k & 1);
+        const int64_t di = ((k + 1) % C == 0) ? CK0 + (k + 1) / C : WK0 + ((k + 1) & 1);
+        rswr_status st = forward_span(k, state0(si), state1(si), state0(di), state1(di));
+        if (st != RSWR_OK) return st;
+    }
+
+    // adjoint sweep
+    RSWR_CUDA(cudaMemsetAsync(state0(LM0), 0, 4 * arr, s));  // both adjoint pairs
+    RSWR_CUDA(adj_init_launch(e->dtype, e->form, state0(LM0), state1(LM0), d_pl, np, wbar, T, s));
+    AdjParams<Real> ap{};
+    ap.prob_u = d_pu;
+    ap.prob_l = d_pl;
+    ap.tiles = d_tiles_a;
+    ap.probes = d_probes;
+    ap.ntiles = nta;
+    ap.H = H;
+    ap.core = core_a;
+    ap.err = e->d_err;
+    ap.wait_ns = (long long)(e->wait_s * 1e9);
+    int cur = 0;
+    for (int64_t g = nck - 1; g >= 0; --g) {
+        const int64_t k_lo = g * C, k_hi = std::min<int64_t>((g + 1) * C, nspans);
+        auto seg = [&](int64_t i) { return i == 0 ? CK0 + g : SG0 + i; };
+        for (int64_t k = k_lo; k + 1 < k_hi; ++k) {
+            const int64_t si = seg(k - k_lo), di = seg(k - k_lo + 1);
+            rswr_status st = forward_span(k, state0(si), state1(si), state0(di), state1(di));
+            if (st != RSWR_OK) return st;
+        }
+        for (int64_t K = k_hi - 1; K >= k_lo; --K) {
+            const int64_t ui = seg(K - k_lo);
+            ap.u0 = state0(ui);
+            ap.u1 = state1(ui);
+            ap.l0 = state0(LM0 + cur);
+            ap.l1 = state1(LM0 + cur);
+            ap.l0_out = state0(LM0 + (cur ^ 1));
+            ap.l1_out = state1(LM0 + (cur ^ 1));
+            ap.n0 = K * SA;
+            ap.len = (int32_t)std::min<int64_t>(SA, T - K * SA);
+            ap.m0 = T - (ap.n0 + ap.len - 1);
+            ap.partial = partial + K * nta;
+            RSWR_CUDA(adj_launch(va, &ap, grid_a, s));
+            cur ^= 1;
+        }
+    }
+    if (grad_a) {
+        if (nspans > 0)
+            RSWR_CUDA(adj_reduce_launch(partial, nspans, nta, d_t0, d_tc, d_scale, grad_a, np, s));
+        else
+            RSWR_CUDA(cudaMemsetAsync(grad_a, 0, sizeof(double) * np, s));
+    }
+    return RSWR_OK;
+}
+
+rswr_status adjoint_dispatch(Engine* e, int64_t T, const int64_t* j_r, const void* fA, const void* fB,
+                             const void* wbar, void* grad, double* grad_a, cudaStream_t s)
+{
+    for (int v = 0; v < adj_variant_count(); ++v) {
+        cudaError_t ce = adj_prepare(v);
+        if (ce != cudaSuccess) return fail(RSWR_ECUDA, std::string("adjoint attributes: ") + cudaGetErrorString(ce));
+    }
+    return e->dtype == kF64 ? adjoint_full<double>(e, T, j_r, fA, fB, wbar, grad, grad_a, s)
+                            : adjoint_full<float>(e, T, j_r, fA, fB, wbar, grad, grad_a, s);
+}
+
+}  // namespace
+
 void rswr::set_error_message(const char* m) { g_msg = m; }
 
 // ===========================================================================
@@ -938,13 +1212,9 @@ rswr_status rswr_adjoint(rswr_plan_t plan, const void* fA, const void* fB, int64
     if (T < 0) return fail(RSWR_EINVAL, "T < 0");
     if (!wbar || !grad_fA) return fail(RSWR_EINVAL, "wbar and grad_fA are required");
     if (j_r < 0 || j_r >= e->probs[0].nx) return fail(RSWR_EINVAL, "receiver index outside the grid");
-    (void)fA;
-    (void)fB;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    rswr_status st = adjoint_g(e, T, &j_r, wbar, grad_fA, s);
-    if (st != RSWR_OK) return st;
-    if (grad_a) return fail(RSWR_ENOTSUP, "dL/da is not available in this build");
-    return RSWR_OK;
+    if (grad_a) return adjoint_dispatch(e, T, &j_r, fA, fB, wbar, grad_fA, grad_a, s);
+    return adjoint_g(e, T, &j_r, wbar, grad_fA, s);
 }
 
 rswr_status rswr_batch_create(rswr_batch_t* batch, int32_t nprob, const rswr_problem* problems, int32_t dtype,
@@ -1055,12 +1325,9 @@ rswr_status rswr_batch_adjoint(rswr_batch_t batch, const void* fA, const void* f
     if (T < 0 || !j_r || !wbar || !grad_fA) return fail(RSWR_EINVAL, "bad argument");
     for (size_t p = 0; p < e->probs.size(); ++p)
         if (j_r[p] < 0 || j_r[p] >= e->probs[p].nx) return fail(RSWR_EINVAL, "receiver index outside the grid");
-    (void)fA;
-    (void)fB;
-    rswr_status st = adjoint_g(e, T, j_r, wbar, grad_fA, static_cast<cudaStream_t>(stream));
-    if (st != RSWR_OK) return st;
-    if (grad_a) return fail(RSWR_ENOTSUP, "dL/da is not available in this build");
-    return RSWR_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (grad_a) return adjoint_dispatch(e, T, j_r, fA, fB, wbar, grad_fA, grad_a, s);
+    return adjoint_g(e, T, j_r, wbar, grad_fA, s);
 }
 
 rswr_status rswr_plan_autotune(rswr_plan_t plan, int64_t probe_steps, int32_t* variant, void* stream)

@@ -90,6 +90,34 @@ struct MonoParams {
     Real k;
 };
 
+// One span of the adjoint sweep over the tiles of an adjoint tiling.  The
+// forward state (u) at level n0 is recomputed for `len` levels inside the
+// kernel; the adjoint state (lambda, run in reversed time) advances from level
+// m0 = T - (n0 + len - 1) by `len` steps.
+template <typename Real>
+struct AdjParams {
+    const ProblemDev<Real>* prob_u;  // forward problem: Dirichlet data, no source
+    const ProblemDev<Real>* prob_l;  // adjoint problem: zero Dirichlet data, source at j_r
+    const TileDev* tiles;            // adjoint tiling (probe ranges: dL/dfA samples)
+    const ProbeDev<Real>* probes;
+    const Real* u0;                  // forward state pair at level n0
+    const Real* u1;
+    const Real* l0;                  // adjoint state pair at level m0
+    const Real* l1;
+    Real* l0_out;                    // adjoint state pair at level m0 + len
+    Real* l1_out;
+    double* partial;                 // [ntiles]: sum over the span of lambda^{n+1}_j lap(u^n)_j on the core
+    int64_t ntiles;
+    int64_t n0;
+    int64_t m0;
+    int32_t len;
+    int32_t H;
+    int32_t core;
+    int32_t pad_;
+    DevError* err;
+    long long wait_ns;
+};
+
 struct VariantInfo {
     int dtype;
     int form;
@@ -104,6 +132,20 @@ size_t span_smem_bytes(int v);
 cudaError_t span_prepare(int v);  // sets the dynamic shared-memory attribute
 cudaError_t span_occupancy(int v, int* blocks_per_sm);
 cudaError_t span_launch(int v, const void* params, int grid, cudaStream_t s);
+
+// adjoint_kernel.cu
+int adj_variant_count();
+VariantInfo adj_variant_info(int v);
+int adj_variant_span(int v);  // largest span the variant's shared-memory store holds
+cudaError_t adj_prepare(int v);
+cudaError_t adj_occupancy(int v, int* blocks_per_sm);
+cudaError_t adj_launch(int v, const void* params, int grid, cudaStream_t s);
+// lambda at level 1 of the reversed-time sweep: wbar[T] at j_r (interior receivers only)
+cudaError_t adj_init_launch(int dtype, int form, void* l0, void* l1, const void* prob_l, int nprob,
+                            const void* wbar, int64_t T, cudaStream_t s);
+// dL/da[p] = 2 c2_p / a_p * sum of the partials of problem p's tiles over all spans
+cudaError_t adj_reduce_launch(const double* partial, int64_t nspans, int64_t ntiles, const int64_t* tile0,
+                              const int64_t* tcount, const double* scale, double* out, int nprob, cudaStream_t s);
 
 // rswr_api.cu: sets the message returned by rswr_last_error_message()
 void set_error_message(const char* m);

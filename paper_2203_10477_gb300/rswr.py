@@ -183,6 +183,7 @@ class Plan:
         self.h = h
         self.nx = nx
         self.n_sub = n_sub
+        self.a = a
 
     @classmethod
     def from_problem(cls, p, dtype=F64, form=FORM_DEFAULT, device=None):
@@ -397,20 +398,30 @@ def _make_function():
     torch = _torch()
 
     class RSWRFunction(torch.autograd.Function):
-        """recv = RSWRFunction.apply(fA, a, plan_args) -- receiver trace of an RSWR
-        run as a differentiable function of the left boundary waveform (and,
-        when the library provides it, of the wave speed a)."""
+        """recv = RSWRFunction.apply(fA, a, plan, T, j_r): the receiver trace of an
+        RSWR run as a differentiable function of the left boundary waveform fA and
+        of the wave speed a (a one-element tensor equal to the plan's speed).
+        Backward calls rswr_adjoint (the library's adjoint kernels)."""
 
         @staticmethod
-        def forward(ctx, fA, plan: Plan, T: int, j_r: int):
-            res = plan.run(fA.detach(), None, T, j_r=j_r)
-            ctx.plan, ctx.T, ctx.j_r = plan, T, j_r
+        def forward(ctx, fA, a, plan: Plan, T: int, j_r: int):
+            if a is not None and abs(float(a) - plan.a) > 1e-15 * max(1.0, abs(plan.a)):
+                raise ValueError("a must equal the plan's wave speed")
+            fA_d = fA.detach()
+            res = plan.run(fA_d, None, T, j_r=j_r)
+            ctx.save_for_backward(fA_d)
+            ctx.plan, ctx.T, ctx.j_r, ctx.want_a = plan, T, j_r, a is not None and a.requires_grad
+            ctx.a_shape = None if a is None else a.shape
             return res["recv"]
 
         @staticmethod
         def backward(ctx, grad_out):
-            g = ctx.plan.adjoint(None, None, ctx.T, ctx.j_r, grad_out.contiguous())
-            return g["grad_fA"], None, None, None
+            (fA,) = ctx.saved_tensors
+            g = ctx.plan.adjoint(fA, None, ctx.T, ctx.j_r, grad_out.contiguous(), want_a=ctx.want_a)
+            ga = None
+            if ctx.want_a:
+                ga = g["grad_a"].reshape(ctx.a_shape).to(grad_out.dtype)
+            return g["grad_fA"], ga, None, None, None
 
     return RSWRFunction
 

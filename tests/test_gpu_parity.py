@@ -286,15 +286,111 @@ def test_autograd_function_matches_oracle(R, oracle_mod):
     a = 1.0
     dt = 0.9 / (nx - 1)
     g = torch.tensor(inputs.lowpass_noise(T, seed=4), dtype=torch.float64, device="cuda", requires_grad=True)
-    target = torch.zeros(T + 1, dtype=torch.float64, device="cuda")
+    at = torch.tensor([a], dtype=torch.float64, device="cuda", requires_grad=True)
+    z = np.zeros(T + 1)
+    target = torch.tensor(oracle_mod.leapfrog(nx, T, 0.9 * a, dt, host(g), z, rec_j=[200])["rec"][0],
+                          dtype=torch.float64, device="cuda")
     plan = R.Plan(0.0, 1.0, a, nx, dt, N, ov, dtype=F64)
     fn = R.rswr_function()
-    tr = fn.apply(g, plan, T, 200)
+    tr = fn.apply(g, at, plan, T, 200)
     loss = ((tr - target) ** 2).sum()
     loss.backward()
-    ref = oracle_mod.misfit_grad(nx, T, a, dt, host(g), np.zeros(T + 1), 200, np.zeros(T + 1))
+    ref = oracle_mod.misfit_grad(nx, T, a, dt, host(g), z, 200, host(target))
     assert abs(loss.item() - ref["loss"]) <= 1e-12 * ref["loss"]
     np.testing.assert_allclose(host(g.grad), ref["dg"], rtol=1e-12, atol=1e-14 * np.abs(ref["dg"]).max())
+    assert abs(at.grad.item() - ref["da"]) <= 1e-12 * ref["abs_da"]
+
+
+# ----------------------------------------------------------------------------
+# adjoint: gradient w.r.t. the wave speed (checkpointed forward, in-SMEM recompute)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nx,N,ov,T,jr", [
+    (301, 3, 16, 420, 120),      # 53 spans of 8 steps, 8 segments
+    (2001, 4, 64, 2003, 777),    # ragged last span, 16 segments
+    (4099, 2, 10, 333, 2000),    # S = 5
+    (301, 3, 16, 420, 0),        # receiver on the Dirichlet node: dL/da = 0
+    (301, 3, 16, 50, 250),       # receiver out of reach: everything 0
+])
+def test_adjoint_grad_a_fp64(R, oracle_mod, nx, N, ov, T, jr):
+    a = 1.3
+    dt = 0.9 / (nx - 1) / a
+    g = inputs.lowpass_noise(T, seed=21)
+    z = np.zeros(T + 1)
+    w = inputs.rng(5).standard_normal(T + 1)
+    plan = R.Plan(0.0, 1.0, a, nx, dt, N, ov, dtype=F64)
+    res = plan.adjoint(g, None, T, jr, w, want_a=True)
+    plan.check()
+    ref = oracle_mod.adjoint(nx, T, a, dt, g, z, jr, w)
+    assert_bitwise(host(res["grad_fA"]), ref["dg"], "grad_fA (checkpointed path)")
+    da = res["grad_a"].item()
+    assert abs(da - ref["da"]) <= 1e-12 * max(ref["abs_da"], 1e-300), (da, ref["da"], ref["abs_da"])
+    if jr == 0 or jr > T + 1:
+        assert da == 0.0
+
+
+def test_adjoint_grad_a_fp32(R, oracle_mod):
+    nx, N, ov, T, jr = 3001, 4, 64, 2000, 1200
+    a = 1.3
+    dt = 0.9 / (nx - 1) / a
+    g = inputs.lowpass_noise(T, seed=2)
+    w = inputs.rng(6).standard_normal(T + 1)
+    plan = R.Plan(0.0, 1.0, a, nx, dt, N, ov, dtype=F32)
+    res = plan.adjoint(g, None, T, jr, w, want_a=True)
+    ref = oracle_mod.adjoint(nx, T, a, dt, g, np.zeros(T + 1), jr, w)
+    da = res["grad_a"].item()
+    assert abs(da - ref["da"]) <= 1e-4 * ref["abs_da"], (da, ref["da"], ref["abs_da"])
+    got = host(res["grad_fA"]).astype(np.float64)
+    assert np.linalg.norm(got - ref["dg"]) <= 1e-4 * np.linalg.norm(ref["dg"])
+
+
+def test_batch_adjoint_with_grad_a(R, oracle_mod):
+    r = inputs.rng(17)
+    T = 400
+    probs, jrs = [], []
+    for i in range(5):
+        nx = int(r.integers(500, 6000))
+        a = float(r.uniform(0.5, 2.0))
+        dt = inputs.dt_for_cfl(nx, a, 0.8)
+        probs.append(inputs.Problem(nx, a, dt, T, max(1, nx // 1024), 32, inputs.lowpass_noise(T, seed=i),
+                                    np.zeros(T + 1)))
+        jrs.append(int(r.integers(1, min(nx - 1, T))))
+    b = R.Batch(probs, dtype=F64)
+    fA = np.concatenate([p.fA for p in probs])
+    w = inputs.rng(18).standard_normal((len(probs), T + 1))
+    res = b.adjoint(fA, None, T, jrs, w, want_a=True)
+    b.check()
+    gf = host(res["grad_fA"])
+    ga = host(res["grad_a"])
+    for i, p in enumerate(probs):
+        ref = oracle_mod.adjoint(p.nx, T, p.a, p.dt, p.fA, p.fB, jrs[i], w[i])
+        assert_bitwise(gf[i], ref["dg"], f"problem {i} grad_fA")
+        assert abs(ga[i] - ref["da"]) <= 1e-12 * ref["abs_da"], (i, ga[i], ref["da"])
+
+
+def test_c4_full_size_adjoint(R, oracle_mod):
+    """Config 4 (nx = 2^20, a = 1.3, CFL 0.9, 8192 steps, N = 256, overlap 64):
+    as written its receiver (x = 0.7) is out of reach, so every gradient is
+    exactly 0; the reachable variant j_r = 4000 is compared with the oracle on
+    the causal prefix of the grid (exact: nothing moves beyond T + 2 points)."""
+    p = inputs.c4()
+    tgt = oracle_mod.leapfrog(p.nx, p.T, 1.0, p.dt, p.fA, p.fB, rec_j=[4000],
+                              nx_run=oracle_mod.causal_extent(p.T, p.nx))["rec"][0]
+    plan = R.Plan.from_problem(p, dtype=F64)
+    # as written: unreachable receiver
+    w0 = inputs.rng(1).standard_normal(p.T + 1)
+    res0 = plan.adjoint(p.fA, None, p.T, p.meta["j_r"], w0, want_a=True)
+    assert float(res0["grad_fA"].abs().max()) == 0.0 and res0["grad_a"].item() == 0.0
+    # reachable variant with the misfit cotangent
+    fw = plan.run(p.fA, None, p.T, j_r=4000)
+    wbar = 2.0 * (host(fw["recv"]) - tgt)
+    res = plan.adjoint(p.fA, None, p.T, 4000, wbar, want_a=True)
+    plan.check()
+    ref = oracle_mod.adjoint(p.nx, p.T, p.a, p.dt, p.fA, p.fB, 4000, wbar,
+                             nx_run=oracle_mod.causal_extent(p.T, p.nx))
+    assert np.abs(ref["dg"]).max() > 0
+    assert_bitwise(host(res["grad_fA"]), ref["dg"], "c4 grad_fA")
+    assert abs(res["grad_a"].item() - ref["da"]) <= 1e-12 * ref["abs_da"]
 
 
 # ----------------------------------------------------------------------------
