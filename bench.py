@@ -281,7 +281,7 @@ def e2e_run(torch, plan, p, steps):
     return ms, h2d, d2h
 
 
-def profile_case(which: str) -> None:
+def profile_case(which: str, variant=None) -> None:
     """The workload of the bench at nx = 2^22 and 320 steps (10 spans): state
     arrays of 32 MiB (FP64) / 16 MiB (FP32) each, four of them, so DRAM counters
     still see traffic beyond L2, and one span-kernel launch of a few ms."""
@@ -292,6 +292,8 @@ def profile_case(which: str) -> None:
     build.build()
     p = inputs.c2(T=320, nx=1 << 22)
     plan = rswr.Plan.from_problem(p, dtype=rswr.F64 if which == "f64" else rswr.F32)
+    if variant is not None:
+        plan.set_variant(variant)
     for _ in range(2):
         plan.run(p.fA, p.fB, p.T, traces=True)
     torch.cuda.synchronize()
@@ -309,10 +311,11 @@ def main():
     ap.add_argument("--no-mono", action="store_true")
     ap.add_argument("--profile-case", choices=["f64", "f32"], default=None,
                     help="run the small profiling case (nx=2^22, 320 steps) twice and exit (for ncu)")
+    ap.add_argument("--variant", type=int, default=None, help="kernel variant of the profiling case")
     args = ap.parse_args()
 
     if args.profile_case:
-        profile_case(args.profile_case)
+        profile_case(args.profile_case, args.variant)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -147,10 +147,19 @@ rswr_status rswr_plan_inject_missing_flag(rswr_plan_t plan, int32_t tile, int32_
  * NULL, NULL clears the hook.  The events stay owned by the caller. */
 rswr_status rswr_plan_set_kernel_events(rswr_plan_t plan, void* start, void* stop);
 
-/* Times every kernel variant of the plan's dtype/form (and both modes) on
- * `probe_steps` steps of a zero-data run and keeps the fastest; returns its
- * index in *variant (may be NULL).  Uses the plan's workspace; synchronous. */
+/* Autotuner: times every kernel variant of the plan's dtype/form (window
+ * width and CTA mapping), both scheduling modes and the spans S = floor(ov/2)
+ * and S/2 on `probe_steps` steps of a zero-data run, and keeps the fastest;
+ * returns its variant index in *variant (may be NULL).  The choice is
+ * remembered per (dtype, form, size class, S) for the process and, when the
+ * environment variable RSWR_AUTOTUNE_CACHE names a file, persisted there and
+ * reused without timing.  Synchronous; uses the plan's workspace. */
 rswr_status rswr_plan_autotune(rswr_plan_t plan, int64_t probe_steps, int32_t* variant, void* stream);
+
+/* Runs are captured into a CUDA graph (on a private stream) the first time a
+ * set of arguments is seen and replayed on `stream` while the arguments stay
+ * the same (default on).  enable = 0 launches every kernel directly. */
+rswr_status rswr_plan_set_graph(rswr_plan_t plan, int32_t enable);
 
 /* Waits for `stream`, then reports a device-side failure latched by the last
  * run (RSWR_ETIMEOUT) or RSWR_OK.  code/tile/span may be NULL. */
@@ -235,6 +244,9 @@ rswr_status rswr_batch_set_mode(rswr_batch_t batch, int32_t mode);
 rswr_status rswr_batch_set_variant(rswr_batch_t batch, int32_t variant);
 rswr_status rswr_batch_set_wait_limit(rswr_batch_t batch, double seconds);
 rswr_status rswr_batch_set_kernel_events(rswr_batch_t batch, void* start, void* stop);
+rswr_status rswr_batch_set_graph(rswr_batch_t batch, int32_t enable);
+/* As rswr_plan_autotune, over the batch's own problems. */
+rswr_status rswr_batch_autotune(rswr_batch_t batch, int64_t probe_steps, int32_t* variant, void* stream);
 rswr_status rswr_batch_check(rswr_batch_t batch, void* stream, int32_t* code, int32_t* tile, int32_t* span);
 
 /* All problems advance T steps in one persistent launch (default mode).

@@ -74,7 +74,7 @@ def _declare(L):
     for suf, R in (("f64", _dbl), ("f32", _flt)):
         f = getattr(L, f"oracle_leapfrog_{suf}")
         f.argtypes = [ctypes.c_int, _i64, _i64, R, R, _vp, _vp, _vp, _vp, _vp, _vp,
-                      _i64, _vp, _vp, _i64, _vp, R, _vp]
+                      _i64, _vp, _vp, _i64, _vp, R, _vp, _i64, _vp]
         f.restype = ctypes.c_int
         g = getattr(L, f"oracle_rswr_mask_{suf}")
         g.argtypes = [ctypes.c_int, _i64, _i64, R, R, _vp, _vp, _vp, _vp, _i64, _i64, _i64,
@@ -132,11 +132,13 @@ def _cf(cf: Coeffs, prec: str):
 
 
 def leapfrog(nx, T, a, dt, fA, fB, *, form=CANONICAL, prec="f64", q0=None, q1=None,
-             rec_j=(), flux_j=(), xa=0.0, xb=1.0, nx_run=None):
+             rec_j=(), flux_j=(), xa=0.0, xb=1.0, nx_run=None, src_j=-1, src=None):
     """Monolithic leapfrog.  Returns dict(u=final q0, w=final q1, rec, flux, coeffs).
 
     The coefficients come from the grid (xa, xb, nx); ``nx_run`` < nx runs the
-    same grid truncated to its first nx_run points (see ``causal_extent``)."""
+    same grid truncated to its first nx_run points (see ``causal_extent``).
+    ``src`` (T+1 values) adds src[n] at the interior point ``src_j`` when level
+    n is formed (the source term of the discrete adjoint)."""
     dt_, suf = _prec(prec)
     cf = coeffs(xa, xb, a, nx, dt)
     nx = nx if nx_run is None else int(nx_run)
@@ -152,9 +154,12 @@ def leapfrog(nx, T, a, dt, fA, fB, *, form=CANONICAL, prec="f64", q0=None, q1=No
     fj = np.ascontiguousarray(flux_j, dtype=np.int64)
     rec = np.empty((len(rj), T + 1), dt_)
     flux = np.empty((len(fj), T + 1), dt_)
+    src = _arr(src, dt_)
+    if src is not None:
+        assert src.shape == (T + 1,)
     rc = getattr(lib(), f"oracle_leapfrog_{suf}")(form, nx, T, c2, k, _ptr(fA), _ptr(fB), _ptr(q0), _ptr(q1),
                                                   _ptr(out0), _ptr(out1), len(rj), _ptr(rj), _ptr(rec),
-                                                  len(fj), _ptr(fj), inv2dx, _ptr(flux))
+                                                  len(fj), _ptr(fj), inv2dx, _ptr(flux), int(src_j), _ptr(src))
     if rc:
         raise RuntimeError(f"oracle_leapfrog failed ({rc})")
     return {"u": out0, "w": out1, "rec": rec, "flux": flux, "coeffs": cf}

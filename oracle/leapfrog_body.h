@@ -85,7 +85,8 @@ int NAME(oracle_leapfrog)(int form, int64_t nx, int64_t T, REAL c2, REAL k,
                           const REAL* fA, const REAL* fB, const REAL* q0, const REAL* q1,
                           REAL* out0, REAL* out1,
                           int64_t nrec, const int64_t* rec_j, REAL* rec,
-                          int64_t nflux, const int64_t* flux_j, REAL inv2dx, REAL* flux)
+                          int64_t nflux, const int64_t* flux_j, REAL inv2dx, REAL* flux,
+                          int64_t src_j, const REAL* src)
 {
     if (nx < 3 || T < 0 || (form != 0 && form != 1)) return 1;
     REAL* u = (REAL*)malloc(sizeof(REAL) * nx);
@@ -98,6 +99,17 @@ int NAME(oracle_leapfrog)(int form, int64_t nx, int64_t T, REAL c2, REAL k,
     for (int64_t n = 0; n < T; ++n) {
         for (int64_t j = 1; j < nx - 1; ++j)
             NAME(point_update)(form, c2, k, u[j - 1], u[j], u[j + 1], w[j], &un[j], &wn[j]);
+        /* optional point source entering level n+1 at src_j (the source term of the
+         * discrete adjoint): added to the new value (form 0) or to the new
+         * increment before it is applied (form 1) */
+        if (src && src_j > 0 && src_j < nx - 1) {
+            if (form == 0) {
+                un[src_j] = un[src_j] + src[n + 1];
+            } else {
+                wn[src_j] = wn[src_j] + src[n + 1];
+                un[src_j] = u[src_j] + wn[src_j];
+            }
+        }
         un[0] = fA[n + 1];
         wn[0] = NAME(dirichlet_w)(form, fA[n], fA[n + 1]);
         un[nx - 1] = fB[n + 1];

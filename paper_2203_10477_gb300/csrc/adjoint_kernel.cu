@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(NT) adjoint_kernel(const __grid_constant__ Adj
                 buf ^= 1;
                 const int64_t m = prm.m0 + s;
                 if (td.probe_end > td.probe_begin)
-                    record_probes<Real, P>(l, lft, rgt, wabs, tid, td.probe_begin, td.probe_end, prm.probes, m);
+                    record_probes<Real, P>(l, lft, rgt, wabs, tid * P, 0, P, td.probe_begin, td.probe_end, prm.probes, m);
                 const Real* lp = laps + (len - 1 - s) * W + tid * P;
 #pragma unroll
                 for (int i = 0; i < P; ++i) {
@@ -243,7 +243,7 @@ AEntry make_aentry()
 {
     constexpr int W = NT * P;
     AEntry e;
-    e.info = VariantInfo{sizeof(Real) == 8 ? kF64 : kF32, FORM, P, NT};
+    e.info = VariantInfo{sizeof(Real) == 8 ? kF64 : kF32, FORM, P, NT, 0, NT * P};
     e.SA = SA;
     e.fn = reinterpret_cast<const void*>(&adjoint_kernel<Real, FORM, P, NT, SA>);
     e.smem = sizeof(Real) * ((4 + SA) * W + 4 * (NT / 32));

@@ -123,7 +123,7 @@ rswr_status run_noalloc(const rswr_problem& q, int form, const void* fA, const v
     }
     if (v < 0) return nfail(RSWR_ENOTSUP, "no kernel variant for this dtype/form");
     const VariantInfo vi = span_variant_info(v);
-    const int W = vi.P * vi.NT;
+    const int W = vi.W;
     const int S = q.overlap / 2 < 256 ? q.overlap / 2 : 256;
     const int H = (S + 3) / 4 * 4;
     const int core = W - 2 * H;

@@ -8,6 +8,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -114,6 +117,11 @@ struct Engine {
     // adjoint workspace (rswr_adjoint with dL/da): states, tables, partial sums
     void* adj_mem = nullptr;
     size_t adj_mem_cap = 0;
+    // CUDA graph of the last run's device work, replayed while the arguments repeat
+    bool use_graph = true;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<int64_t> graph_key;
 
     size_t esize() const { return dtype == kF64 ? 8 : 4; }
 };
@@ -136,6 +144,8 @@ void free_engine(Engine* e)
     cudaFree(e->d_err);
     cudaFree(e->d_host_stage);
     cudaFree(e->adj_mem);
+    if (e->graph_exec) cudaGraphExecDestroy(e->graph_exec);
+    if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
     delete e;
 }
 
@@ -156,7 +166,7 @@ rswr_status layout(Engine* e)
     const VariantInfo vi = span_variant_info(e->variant);
     e->P = vi.P;
     e->NT = vi.NT;
-    e->W = vi.P * vi.NT;
+    e->W = vi.W;
     e->H = (e->S + 3) / 4 * 4;
     e->core = e->W - 2 * e->H;
     if (e->core < e->H || e->core < 4) return fail(RSWR_EINVAL, "span too long for the CTA window of this variant");
@@ -270,6 +280,7 @@ rswr_status make_engine(Engine** out, int nprob, const rswr_problem* pr, int32_t
     if (ce == cudaSuccess) ce = cudaMalloc(&e->d_ticket, sizeof(unsigned long long));
     if (ce == cudaSuccess) ce = cudaMalloc(&e->d_err, sizeof(DevError));
     if (ce == cudaSuccess) ce = cudaMemset(e->d_err, 0, sizeof(DevError));
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking);
     if (ce != cudaSuccess) {
         free_engine(e);
         return fail(RSWR_ECUDA, std::string("engine setup: ") + cudaGetErrorString(ce));
@@ -490,15 +501,21 @@ SpanParams<Real> span_params(Engine* e, int64_t T, int nspans)
 }
 
 template <typename Real>
-rswr_status run_impl(Engine* e, const RunReq& r, cudaStream_t s)
+rswr_status prepare_tables(Engine* e, const RunReq& r, int* nprobe, cudaStream_t s)
 {
-    const size_t es = sizeof(Real);
-    RSWR_CUDA(cudaMemsetAsync(e->d_err, 0, sizeof(DevError), s));
     rswr_status st = upload_problems<Real>(e, r, s);
     if (st != RSWR_OK) return st;
-    int nprobe = 0;
-    st = upload_probes<Real>(e, r, &nprobe, s);
-    if (st != RSWR_OK) return st;
+    return upload_probes<Real>(e, r, nprobe, s);
+}
+
+// The device work of one run (capturable in a CUDA graph: no host sync, no
+// host-to-device copies).
+template <typename Real>
+rswr_status device_work(Engine* e, const RunReq& r, int nprobe, cudaStream_t s)
+{
+    const size_t es = sizeof(Real);
+    rswr_status st = RSWR_OK;
+    RSWR_CUDA(cudaMemsetAsync(e->d_err, 0, sizeof(DevError), s));
 
     // level-0 state into buffer 0
     if (!r.q0) {
@@ -518,7 +535,7 @@ rswr_status run_impl(Engine* e, const RunReq& r, cudaStream_t s)
 
     const void* fin0;
     const void* fin1;
-    if (e->ev_start) RSWR_CUDA(cudaEventRecord(e->ev_start, s));
+    if (e->ev_start) RSWR_CUDA(cudaEventRecordWithFlags(e->ev_start, s, cudaEventRecordExternal));
     if (!r.mono) {
         const int nspans = (int)((r.T + e->S - 1) / e->S);
         SpanParams<Real> prm = span_params<Real>(e, r.T, nspans);
@@ -582,11 +599,70 @@ rswr_status run_impl(Engine* e, const RunReq& r, cudaStream_t s)
             fin1 = b;
         }
     }
-    if (e->ev_stop) RSWR_CUDA(cudaEventRecord(e->ev_stop, s));
+    if (e->ev_stop) RSWR_CUDA(cudaEventRecordWithFlags(e->ev_stop, s, cudaEventRecordExternal));
     RSWR_CUDA(probe_final_launch(e->dtype, e->d_probes, nprobe, fin0, r.T, s));
     if (r.out0 && (st = pack<Real>(e, r.out0, fin0, s)) != RSWR_OK) return st;
     if (r.out1 && (st = pack<Real>(e, r.out1, fin1, s)) != RSWR_OK) return st;
     return RSWR_OK;
+}
+
+// Everything that determines the device work of a run.
+std::vector<int64_t> run_key(const Engine* e, const RunReq& r)
+{
+    auto P = [](const void* p) { return (int64_t)(intptr_t)p; };
+    std::vector<int64_t> k{r.mono, P(r.fA), P(r.fB), r.T, P(r.q0), P(r.q1), P(r.out0), P(r.out1), P(r.src),
+                           r.src_pitch, r.src_stride, e->variant, e->mode, e->S, e->H, P(e->ev_start),
+                           P(e->ev_stop), e->inject_tile, e->inject_span, (int64_t)(e->wait_s * 1e3),
+                           (int64_t)r.probes.size()};
+    for (const ProbeReq& q : r.probes) {
+        k.insert(k.end(), {q.p, q.j, q.kind, P(q.out), q.stride, q.nmax, q.scale_is_c2});
+        int64_t sb;
+        std::memcpy(&sb, &q.scale, sizeof(sb));
+        k.push_back(sb);
+    }
+    k.insert(k.end(), r.js.begin(), r.js.end());
+    return k;
+}
+
+template <typename Real>
+rswr_status run_graph(Engine* e, const RunReq& r, int nprobe, cudaStream_t s)
+{
+    std::vector<int64_t> key = run_key(e, r);
+    if (!e->graph_exec || key != e->graph_key) {
+        if (e->graph_exec) {
+            cudaGraphExecDestroy(e->graph_exec);
+            e->graph_exec = nullptr;
+        }
+        e->graph_key.clear();
+        RSWR_CUDA(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
+        rswr_status st = device_work<Real>(e, r, nprobe, e->cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(e->cap_stream, &g);
+        if (st != RSWR_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (ce != cudaSuccess) return fail(RSWR_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&e->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) {
+            e->graph_exec = nullptr;
+            return fail(RSWR_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+        }
+        e->graph_key = key;
+    }
+    RSWR_CUDA(cudaGraphLaunch(e->graph_exec, s));
+    return RSWR_OK;
+}
+
+template <typename Real>
+rswr_status run_impl(Engine* e, const RunReq& r, cudaStream_t s)
+{
+    int nprobe = 0;
+    rswr_status st = prepare_tables<Real>(e, r, &nprobe, s);
+    if (st != RSWR_OK) return st;
+    if (e->use_graph) return run_graph<Real>(e, r, nprobe, s);
+    return device_work<Real>(e, r, nprobe, s);
 }
 
 rswr_status run_engine(Engine* e, const RunReq& r, cudaStream_t s)
@@ -774,8 +850,8 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     const int H = (SA + 3) / 4 * 4;
     const int vf = e->variant;
     const VariantInfo fi = span_variant_info(vf);
-    const int core_f = fi.P * fi.NT - 2 * H;
-    const int core_a = ai.P * ai.NT - 2 * H;
+    const int core_f = fi.W - 2 * H;
+    const int core_a = ai.W - 2 * H;
     if (core_f < H || core_a < H) return fail(RSWR_EINVAL, "adjoint tiling: window too small");
     const int64_t pad = H + 8;
 
@@ -1011,6 +1087,156 @@ rswr_status adjoint_dispatch(Engine* e, int64_t T, const int64_t* j_r, const voi
     }
     return e->dtype == kF64 ? adjoint_full<double>(e, T, j_r, fA, fB, wbar, grad, grad_a, s)
                             : adjoint_full<float>(e, T, j_r, fA, fB, wbar, grad, grad_a, s);
+}
+
+}  // namespace
+
+namespace {
+
+// ---- autotuner -----------------------------------------------------------
+// Times every kernel variant of the engine's dtype/form, both scheduling modes
+// and spans S and S/2 on `probe_steps` steps of a zero-data run of the
+// engine's own problems, keeps the fastest, and remembers it per
+// (dtype, form, log2 points, problems, S) in a process-wide table that can be
+// persisted to the file named by RSWR_AUTOTUNE_CACHE.
+
+struct TuneChoice {
+    int variant, mode, S;
+};
+
+std::mutex g_tune_mu;
+std::map<std::string, TuneChoice> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_key(const Engine* e, int S_max)
+{
+    int64_t n = e->packed_len;
+    int lg = 0;
+    while ((int64_t(1) << (lg + 1)) <= n) ++lg;
+    return std::to_string(e->dtype) + ":" + std::to_string(e->form) + ":" + std::to_string(lg) + ":" +
+           std::to_string(e->probs.size() > 1 ? 1 : 0) + ":" + std::to_string(S_max);
+}
+
+void tune_load()
+{
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* path = std::getenv("RSWR_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return;
+    char key[128];
+    int v, m, S;
+    while (std::fscanf(f, "%127s %d %d %d", key, &v, &m, &S) == 4) g_tune[key] = TuneChoice{v, m, S};
+    std::fclose(f);
+}
+
+void tune_save()
+{
+    const char* path = std::getenv("RSWR_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "w");
+    if (!f) return;
+    for (const auto& kv : g_tune) std::fprintf(f, "%s %d %d %d\n", kv.first.c_str(), kv.second.variant, kv.second.mode, kv.second.S);
+    std::fclose(f);
+}
+
+rswr_status apply_choice(Engine* e, const TuneChoice& c)
+{
+    const int oldS = e->S, oldV = e->variant;
+    e->S = c.S;
+    e->variant = c.variant;
+    rswr_status st = layout(e);
+    if (st != RSWR_OK) {
+        e->S = oldS;
+        e->variant = oldV;
+        layout(e);
+        return st;
+    }
+    e->mode = c.mode;
+    return RSWR_OK;
+}
+
+int span_limit(const Engine* e)
+{
+    int S = 1 << 30;
+    for (const ProbHost& p : e->probs) S = std::min(S, p.ov / 2);
+    return std::min(S, kSpanCap);
+}
+
+rswr_status autotune_engine(Engine* e, int64_t probe_steps, int32_t* variant, cudaStream_t s, bool use_cache)
+{
+    if (probe_steps < 1) return fail(RSWR_EINVAL, "probe_steps must be >= 1");
+    const int S_max = span_limit(e);
+    const std::string key = tune_key(e, S_max);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        tune_load();
+        auto it = g_tune.find(key);
+        if (use_cache && it != g_tune.end()) {
+            rswr_status st = apply_choice(e, it->second);
+            if (st == RSWR_OK) {
+                if (variant) *variant = e->variant;
+                return RSWR_OK;
+            }
+        }
+    }
+    const size_t es = e->esize();
+    if (e->scratch_cap < (size_t)e->packed_len) {
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(e->d_scratch[b]);
+            e->d_scratch[b] = nullptr;
+            if (cudaMalloc(&e->d_scratch[b], es * e->packed_len) != cudaSuccess) return fail(RSWR_ENOMEM, "scratch");
+        }
+        e->scratch_cap = e->packed_len;
+    }
+    cudaEvent_t a, b;
+    RSWR_CUDA(cudaEventCreate(&a));
+    RSWR_CUDA(cudaEventCreate(&b));
+    const cudaEvent_t keep0 = e->ev_start, keep1 = e->ev_stop;
+    e->ev_start = e->ev_stop = nullptr;
+    const TuneChoice keep{e->variant, e->mode, e->S};
+    TuneChoice best = keep;
+    float best_ms = 1e30f;
+    RunReq r;
+    r.T = probe_steps;
+    r.out0 = e->d_scratch[0];
+    r.out1 = e->d_scratch[1];
+    std::vector<int> spans{S_max};
+    if (S_max / 2 >= 4) spans.push_back(S_max / 2);
+    for (int v = 0; v < span_variant_count(); ++v) {
+        const VariantInfo vi = span_variant_info(v);
+        if (vi.dtype != e->dtype || vi.form != e->form) continue;
+        for (int S : spans) {
+            for (int mode = 0; mode < 2; ++mode) {
+                if (apply_choice(e, TuneChoice{v, mode, S}) != RSWR_OK) continue;
+                if (run_engine(e, r, s) != RSWR_OK) continue;  // warm-up (and graph capture)
+                RSWR_CUDA(cudaEventRecord(a, s));
+                rswr_status st = run_engine(e, r, s);
+                RSWR_CUDA(cudaEventRecord(b, s));
+                RSWR_CUDA(cudaEventSynchronize(b));
+                float ms = 0.f;
+                RSWR_CUDA(cudaEventElapsedTime(&ms, a, b));
+                if (st == RSWR_OK && ms < best_ms) {
+                    best_ms = ms;
+                    best = TuneChoice{v, mode, S};
+                }
+            }
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    e->ev_start = keep0;
+    e->ev_stop = keep1;
+    rswr_status st = apply_choice(e, best);
+    if (st != RSWR_OK) return st;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune[key] = best;
+        tune_save();
+    }
+    if (variant) *variant = e->variant;
+    return RSWR_OK;
 }
 
 }  // namespace
@@ -1333,55 +1559,27 @@ rswr_status rswr_batch_adjoint(rswr_batch_t batch, const void* fA, const void* f
 rswr_status rswr_plan_autotune(rswr_plan_t plan, int64_t probe_steps, int32_t* variant, void* stream)
 {
     if (!plan) return fail(RSWR_EINVAL, "NULL plan");
-    Engine* e = plan->e;
-    if (probe_steps < 1) return fail(RSWR_EINVAL, "probe_steps must be >= 1");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int64_t nx = e->probs[0].nx;
-    const size_t es = e->esize();
-    if (e->scratch_cap < (size_t)nx) {
-        for (int b = 0; b < 2; ++b) {
-            cudaFree(e->d_scratch[b]);
-            e->d_scratch[b] = nullptr;
-            if (cudaMalloc(&e->d_scratch[b], es * nx) != cudaSuccess) return fail(RSWR_ENOMEM, "scratch");
-        }
-        e->scratch_cap = nx;
-    }
-    cudaEvent_t a, b;
-    RSWR_CUDA(cudaEventCreate(&a));
-    RSWR_CUDA(cudaEventCreate(&b));
-    float best = 1e30f;
-    int best_v = e->variant, best_mode = e->mode;
-    const int keep_mode = e->mode;
-    for (int v = 0; v < span_variant_count(); ++v) {
-        const VariantInfo vi = span_variant_info(v);
-        if (vi.dtype != e->dtype || vi.form != e->form) continue;
-        if (set_variant(e, v) != RSWR_OK) continue;
-        for (int mode = 0; mode < 2; ++mode) {
-            e->mode = mode;
-            rswr_status st = plan_run(e, nullptr, nullptr, probe_steps, nullptr, nullptr, e->d_scratch[0],
-                                      e->d_scratch[1], nullptr, 0, nullptr, stream, false);  // warm-up
-            if (st != RSWR_OK) continue;
-            RSWR_CUDA(cudaEventRecord(a, s));
-            st = plan_run(e, nullptr, nullptr, probe_steps, nullptr, nullptr, e->d_scratch[0], e->d_scratch[1],
-                          nullptr, 0, nullptr, stream, false);
-            RSWR_CUDA(cudaEventRecord(b, s));
-            RSWR_CUDA(cudaEventSynchronize(b));
-            float ms = 0.f;
-            RSWR_CUDA(cudaEventElapsedTime(&ms, a, b));
-            if (st == RSWR_OK && ms < best) {
-                best = ms;
-                best_v = v;
-                best_mode = mode;
-            }
-        }
-    }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    e->mode = keep_mode;
-    rswr_status st = set_variant(e, best_v);
-    e->mode = best_mode;
-    if (variant) *variant = best_v;
-    return st;
+    return autotune_engine(plan->e, probe_steps, variant, static_cast<cudaStream_t>(stream), true);
+}
+
+rswr_status rswr_batch_autotune(rswr_batch_t batch, int64_t probe_steps, int32_t* variant, void* stream)
+{
+    if (!batch) return fail(RSWR_EINVAL, "NULL batch");
+    return autotune_engine(batch->e, probe_steps, variant, static_cast<cudaStream_t>(stream), true);
+}
+
+rswr_status rswr_plan_set_graph(rswr_plan_t plan, int32_t enable)
+{
+    if (!plan) return fail(RSWR_EINVAL, "NULL plan");
+    plan->e->use_graph = enable != 0;
+    return RSWR_OK;
+}
+
+rswr_status rswr_batch_set_graph(rswr_batch_t batch, int32_t enable)
+{
+    if (!batch) return fail(RSWR_EINVAL, "NULL batch");
+    batch->e->use_graph = enable != 0;
+    return RSWR_OK;
 }
 
 int32_t rswr_variant_count(void) { return span_variant_count(); }

@@ -121,8 +121,10 @@ struct AdjParams {
 struct VariantInfo {
     int dtype;
     int form;
-    int P;
-    int NT;
+    int P;   // points per thread
+    int NT;  // threads per CTA
+    int KH;  // warp halo (0: warps exchange neighbours every step)
+    int W;   // points per CTA window
 };
 
 // span_kernel.cu

@@ -166,15 +166,78 @@ __device__ __forceinline__ void patch_special(Real (&u)[P], Real (&w)[P], const 
     }
 }
 
+// The same step as exchange() + leap_step(), reordered to hide the halo
+// latency: the thread posts its edge values (shuffles + shared slots), updates
+// its interior points 1..P-2, waits at the block barrier, then fetches the
+// cross-warp halos and updates points 0 and P-1.  Every update is the same
+// expression on the same operands as leap_step(), so the bits are identical.
+template <typename Real, int FORM, int P, int NW>
+__device__ __forceinline__ void split_step(Real (&u)[P], Real (&w)[P], Real c2, Real k, Real* xch, int buf,
+                                           int warp, int lane)
+{
+    static_assert(P >= 3, "split step needs interior points");
+    Real lft = __shfl_up_sync(kFull, u[P - 1], 1);
+    Real rgt = __shfl_down_sync(kFull, u[0], 1);
+    Real* slot = xch + buf * NW * 2;
+    if (lane == 0) slot[warp * 2 + 0] = u[0];
+    if (lane == 31) slot[warp * 2 + 1] = u[P - 1];
+    const Real m_l = u[1];      // mirror ghosts at the window ends (zero-flux guess)
+    const Real m_r = u[P - 2];
+    if constexpr (FORM == kIncrement) {
+        const Real d0 = rsub(u[1], u[0]);
+        Real dprev = d0;
+#pragma unroll
+        for (int i = 1; i < P - 1; ++i) {
+            const Real d = rsub(u[i + 1], u[i]);
+            const Real v = rfma(c2, rsub(d, dprev), w[i]);
+            dprev = d;
+            w[i] = v;
+            u[i] = radd(u[i], v);
+        }
+        __syncthreads();
+        if (lane == 0) lft = (warp > 0) ? slot[(warp - 1) * 2 + 1] : m_l;
+        if (lane == 31) rgt = (warp < NW - 1) ? slot[(warp + 1) * 2 + 0] : m_r;
+        {
+            const Real v = rfma(c2, rsub(d0, rsub(u[0], lft)), w[0]);
+            w[0] = v;
+            u[0] = radd(u[0], v);
+        }
+        {
+            const Real v = rfma(c2, rsub(rsub(rgt, u[P - 1]), dprev), w[P - 1]);
+            w[P - 1] = v;
+            u[P - 1] = radd(u[P - 1], v);
+        }
+    } else {
+        const Real u0 = u[0], uP1 = u[P - 1];
+        Real ul = u0;
+#pragma unroll
+        for (int i = 1; i < P - 1; ++i) {
+            const Real uc = u[i];
+            const Real un = rfma(c2, radd(ul, u[i + 1]), rfma(k, uc, -w[i]));
+            w[i] = uc;
+            u[i] = un;
+            ul = uc;
+        }
+        __syncthreads();
+        if (lane == 0) lft = (warp > 0) ? slot[(warp - 1) * 2 + 1] : m_l;
+        if (lane == 31) rgt = (warp < NW - 1) ? slot[(warp + 1) * 2 + 0] : m_r;
+        u[0] = rfma(c2, radd(lft, m_l), rfma(k, u0, -w[0]));
+        w[0] = u0;
+        u[P - 1] = rfma(c2, radd(ul, rgt), rfma(k, uP1, -w[P - 1]));
+        w[P - 1] = uP1;
+    }
+}
+
 // Interface output waveforms and receiver samples of level n (recorded before
-// the step that leaves level n).  Only the owner thread of a point writes.
+// the step that leaves level n).  Only the owner thread of a point writes: the
+// thread whose first point sits at window index tb, registers [rlo, rhi).
 template <typename Real, int P>
-__device__ __forceinline__ void record_probes(const Real (&u)[P], Real lft, Real rgt, int64_t wabs, int tid,
-                                              int pb, int pe, const ProbeDev<Real>* probes, int64_t n)
+__device__ __forceinline__ void record_probes(const Real (&u)[P], Real lft, Real rgt, int64_t wabs, int tb, int rlo,
+                                              int rhi, int pb, int pe, const ProbeDev<Real>* probes, int64_t n)
 {
     for (int q = pb; q < pe; ++q) {
-        const int64_t li = probes[q].gidx - wabs - (int64_t)tid * P;
-        if (li < 0 || li >= P) continue;
+        const int64_t li = probes[q].gidx - wabs - (int64_t)tb;
+        if (li < rlo || li >= rhi) continue;
         const int r = (int)li;
         Real um = lft, uc = u[0], up = rgt;
 #pragma unroll
@@ -189,6 +252,248 @@ __device__ __forceinline__ void record_probes(const Real (&u)[P], Real lft, Real
         Real val = (pr.kind == 0) ? uc : rsub(up, um);
         val = rmul(val, pr.scale);
         if (n <= pr.nmax) pr.out[n * pr.stride] = val;
+    }
+}
+
+// A tile's probes staged in shared memory once per tile; each thread keeps the
+// indices of (at most two) probes whose point it owns.
+constexpr int kTileProbes = 16;
+
+template <typename Real, int P>
+__device__ __forceinline__ void owned_probes(const ProbeDev<Real>* sp, int np, int64_t wabs, int tb, int rlo, int rhi,
+                                             int& q0, int& q1)
+{
+    q0 = -1;
+    q1 = -1;
+    for (int q = 0; q < np; ++q) {
+        const int64_t li = sp[q].gidx - wabs - (int64_t)tb;
+        if (li >= rlo && li < rhi) {
+            if (q0 < 0) q0 = q;
+            else q1 = q;
+        }
+    }
+}
+
+template <typename Real, int P>
+__device__ __forceinline__ void record_owned(const Real (&u)[P], Real lft, Real rgt, const ProbeDev<Real>& pr,
+                                             int64_t wabs, int tb, int64_t n)
+{
+    const int r = (int)(pr.gidx - wabs - (int64_t)tb);
+    Real um = lft, uc = u[0], up = rgt;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        if (i == r) {
+            uc = u[i];
+            um = (i > 0) ? u[i - 1] : lft;
+            up = (i < P - 1) ? u[i + 1] : rgt;
+        }
+    }
+    Real val = (pr.kind == 0) ? uc : rsub(up, um);
+    val = rmul(val, pr.scale);
+    if (n <= pr.nmax) pr.out[n * pr.stride] = val;
+}
+
+// Overlapping warp windows (KH > 0): warp w covers window points
+// [w (32P - 2KH), w (32P - 2KH) + 32P) and owns all but KH points at each end.
+// Every KH steps the halo points are refreshed from the neighbours' owned
+// points through shared memory (double-buffered slots, one block barrier);
+// in between, warps advance with shuffles only and the contamination from
+// their window ends stays inside the halos.
+template <typename Real, int P, int NW, int KH>
+__device__ __forceinline__ void refresh_halos(Real (&u)[P], Real (&w)[P], Real* hx, int buf, int warp, int lane)
+{
+    static_assert(P >= 2 * KH, "a thread must hold a halo and the owned points next to it");
+    using V = typename Vec<Real, P>::T;
+    constexpr int N = Vec<Real, P>::N;
+    static_assert(KH % N == 0, "halo width must fill whole vectors");
+    // slots: [buffer][warp][side: 0 = first owned, 1 = last owned][component][KH], vector aligned
+    Real* b = hx + buf * NW * 4 * KH;
+    if (lane == 0 || lane == 31) {
+        const int side = lane == 0 ? 0 : 1;
+        V* su = reinterpret_cast<V*>(b + ((warp * 2 + side) * 2 + 0) * KH);
+        V* sw = reinterpret_cast<V*>(b + ((warp * 2 + side) * 2 + 1) * KH);
+#pragma unroll
+        for (int k = 0; k < KH / N; ++k) {
+            V vu, vw;
+            const int o = (lane == 0) ? KH + k * N : P - 2 * KH + k * N;
+            if constexpr (N == 4) {
+                vu = lane == 0 ? V{u[KH + 4 * k], u[KH + 4 * k + 1], u[KH + 4 * k + 2], u[KH + 4 * k + 3]}
+                               : V{u[P - 2 * KH + 4 * k], u[P - 2 * KH + 4 * k + 1], u[P - 2 * KH + 4 * k + 2],
+                                   u[P - 2 * KH + 4 * k + 3]};
+                vw = lane == 0 ? V{w[KH + 4 * k], w[KH + 4 * k + 1], w[KH + 4 * k + 2], w[KH + 4 * k + 3]}
+                               : V{w[P - 2 * KH + 4 * k], w[P - 2 * KH + 4 * k + 1], w[P - 2 * KH + 4 * k + 2],
+                                   w[P - 2 * KH + 4 * k + 3]};
+            } else {
+                vu = lane == 0 ? V{u[KH + 2 * k], u[KH + 2 * k + 1]} : V{u[P - 2 * KH + 2 * k], u[P - 2 * KH + 2 * k + 1]};
+                vw = lane == 0 ? V{w[KH + 2 * k], w[KH + 2 * k + 1]} : V{w[P - 2 * KH + 2 * k], w[P - 2 * KH + 2 * k + 1]};
+            }
+            (void)o;
+            su[k] = vu;
+            sw[k] = vw;
+        }
+    }
+    __syncthreads();
+    if ((lane == 0 && warp > 0) || (lane == 31 && warp < NW - 1)) {
+        const int src = lane == 0 ? ((warp - 1) * 2 + 1) : ((warp + 1) * 2 + 0);
+        const V* su = reinterpret_cast<const V*>(b + (src * 2 + 0) * KH);
+        const V* sw = reinterpret_cast<const V*>(b + (src * 2 + 1) * KH);
+#pragma unroll
+        for (int k = 0; k < KH / N; ++k) {
+            const V vu = su[k], vw = sw[k];
+            if (lane == 0) {
+                if constexpr (N == 4) {
+                    u[4 * k] = vu.x; u[4 * k + 1] = vu.y; u[4 * k + 2] = vu.z; u[4 * k + 3] = vu.w;
+                    w[4 * k] = vw.x; w[4 * k + 1] = vw.y; w[4 * k + 2] = vw.z; w[4 * k + 3] = vw.w;
+                } else {
+                    u[2 * k] = vu.x; u[2 * k + 1] = vu.y;
+                    w[2 * k] = vw.x; w[2 * k + 1] = vw.y;
+                }
+            } else {
+                if constexpr (N == 4) {
+                    u[P - KH + 4 * k] = vu.x; u[P - KH + 4 * k + 1] = vu.y; u[P - KH + 4 * k + 2] = vu.z;
+                    u[P - KH + 4 * k + 3] = vu.w;
+                    w[P - KH + 4 * k] = vw.x; w[P - KH + 4 * k + 1] = vw.y; w[P - KH + 4 * k + 2] = vw.z;
+                    w[P - KH + 4 * k + 3] = vw.w;
+                } else {
+                    u[P - KH + 2 * k] = vu.x; u[P - KH + 2 * k + 1] = vu.y;
+                    w[P - KH + 2 * k] = vw.x; w[P - KH + 2 * k + 1] = vw.y;
+                }
+            }
+        }
+    }
+}
+
+// Neighbour values inside a warp window (shuffles; mirror ghost at its ends).
+template <typename Real, int P>
+__device__ __forceinline__ void warp_neighbours(const Real (&u)[P], Real& lft, Real& rgt, int lane)
+{
+    lft = __shfl_up_sync(kFull, u[P - 1], 1);
+    rgt = __shfl_down_sync(kFull, u[0], 1);
+    if (lane == 0) lft = u[1];
+    if (lane == 31) rgt = u[P - 2];
+}
+
+// Write the registers a thread owns, [own_lo, own_hi), back to the shared window.
+template <typename Real, int P, int KH>
+__device__ __forceinline__ void owned_to_smem(Real* s, const Real (&r)[P], int own_lo, int own_hi)
+{
+    if (KH == 0 || (own_lo == 0 && own_hi == P)) {
+        regs_to_smem<Real, P>(s, r);
+    } else {
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+            if (i >= own_lo && i < own_hi) s[i] = r[i];
+    }
+}
+
+// ---- packed FP32 (sm_100+ f32x2): two points per instruction ----------------
+// A thread's P points are two half blocks A = [0, P/2) and B = [P/2, P); pair i
+// holds (A[i], B[i]) in one 64-bit register, so a pair's neighbours are pairs
+// i-1 and i+1 and every packed operation is, lane by lane, the scalar one.
+
+__device__ __forceinline__ uint64_t pk2(float lo, float hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float lo2(uint64_t v)
+{
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return lo;
+}
+__device__ __forceinline__ float hi2(uint64_t v)
+{
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return hi;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// Point j of a thread in the packed layout.
+template <int P>
+__device__ __forceinline__ float pget(const uint64_t (&U)[P / 2], int j)
+{
+    return j < P / 2 ? lo2(U[j]) : hi2(U[j - P / 2]);
+}
+
+// `steps` increment-form leapfrog steps of one thread's P points held packed,
+// with warp halos of KH points refreshed every KH steps (as refresh_halos).
+// Interior tiles only: no Dirichlet nodes, sources or probes.
+template <int P, int NW, int KH>
+__device__ __forceinline__ void packed_increment_steps(float (&u)[P], float (&w)[P], float c2, int steps, float* hx,
+                                                       int& buf, int warp, int lane)
+{
+    constexpr int H2 = P / 2;
+    static_assert(P % 2 == 0 && H2 >= 2, "packed layout needs an even number of points");
+    uint64_t U[H2], V[H2];
+#pragma unroll
+    for (int i = 0; i < H2; ++i) {
+        U[i] = pk2(u[i], u[H2 + i]);
+        V[i] = pk2(w[i], w[H2 + i]);
+    }
+    const uint64_t c2p = pk2(c2, c2);
+    for (int s0 = 0; s0 < steps; s0 += KH) {
+        if (s0 > 0) {
+            // unpack the halo-relevant points, refresh, repack (KH <= P/2 points per side)
+#pragma unroll
+            for (int i = 0; i < H2; ++i) {
+                u[i] = lo2(U[i]);
+                u[H2 + i] = hi2(U[i]);
+                w[i] = lo2(V[i]);
+                w[H2 + i] = hi2(V[i]);
+            }
+            refresh_halos<float, P, NW, KH>(u, w, hx, buf, warp, lane);
+            buf ^= 1;
+#pragma unroll
+            for (int i = 0; i < H2; ++i) {
+                U[i] = pk2(u[i], u[H2 + i]);
+                V[i] = pk2(w[i], w[H2 + i]);
+            }
+        }
+        const int s1 = (s0 + KH < steps) ? s0 + KH : steps;
+        for (int s = s0; s < s1; ++s) {
+            float lft = __shfl_up_sync(kFull, hi2(U[H2 - 1]), 1);  // previous thread's last point
+            float rgt = __shfl_down_sync(kFull, lo2(U[0]), 1);     // next thread's first point
+            if (lane == 0) lft = lo2(U[1]);                         // mirror at the warp window ends
+            if (lane == 31) rgt = hi2(U[H2 - 2]);
+            const uint64_t Lp = pk2(lft, lo2(U[H2 - 1]));  // left neighbours of pair 0
+            const uint64_t Rp = pk2(hi2(U[0]), rgt);       // right neighbours of pair H2-1
+            uint64_t dprev = sub2(U[0], Lp);
+#pragma unroll
+            for (int i = 0; i < H2; ++i) {
+                const uint64_t d = sub2(i < H2 - 1 ? U[i + 1] : Rp, U[i]);
+                const uint64_t v = fma2(c2p, sub2(d, dprev), V[i]);
+                dprev = d;
+                V[i] = v;
+                U[i] = add2(U[i], v);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < H2; ++i) {
+        u[i] = lo2(U[i]);
+        u[H2 + i] = hi2(U[i]);
+        w[i] = lo2(V[i]);
+        w[H2 + i] = hi2(V[i]);
     }
 }
 

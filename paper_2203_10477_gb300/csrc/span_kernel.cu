@@ -119,17 +119,31 @@ __device__ __forceinline__ void publish(const SpanParams<Real>& prm, long long t
 
 }  // namespace
 
-template <typename Real, int FORM, int P, int NT>
-__global__ void __launch_bounds__(NT, 2) span_kernel(const __grid_constant__ SpanParams<Real> prm)
+// Window geometry of a variant: KH = 0 -> warps tile the window back to back;
+// KH > 0 -> warp windows overlap by 2 KH points (see refresh_halos).
+template <int P, int NT, int KH>
+struct Geom {
+    static constexpr int NW = NT / 32;
+    static constexpr int CW = KH == 0 ? 32 * P : 32 * P - 2 * KH;  // window offset between warps
+    static constexpr int W = KH == 0 ? NT * P : NW * CW + 2 * KH;   // points per CTA window
+    static constexpr int XCH = ((4 * NW + 15) / 16) * 16 + 8 * NW * KH;  // exchange slots (values)
+};
+
+template <typename Real, int FORM, int P, int NT, int KH, int PK, int MINB>
+__global__ void __launch_bounds__(NT, MINB) span_kernel(const __grid_constant__ SpanParams<Real> prm)
 {
-    constexpr int W = NT * P;
-    constexpr int NW = NT / 32;
+    using G = Geom<P, NT, KH>;
+    constexpr int W = G::W;
+    constexpr int NW = G::NW;
+    static_assert(W % 4 == 0, "windows must span whole 16-byte units");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Real* stage = reinterpret_cast<Real*>(smem_raw);  // [2 stages][2 components][W]
-    Real* xch = stage + 4 * W;                        // [2 buffers][NW][2]
+    Real* xch = stage + 4 * W;                        // [2 buffers][NW][2]  (+ halo slots when KH > 0)
+    Real* hx = xch + ((4 * NW + 15) / 16) * 16;  // vector-aligned halo slots
     __shared__ __align__(8) uint64_t full_bar[2];
     __shared__ long long s_ticket[2];
     __shared__ int s_abort;
+    __shared__ ProbeDev<Real> s_probes[kTileProbes];
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -211,13 +225,28 @@ __global__ void __launch_bounds__(NT, 2) span_kernel(const __grid_constant__ Spa
         const bool slow = edge || has_src;
         const bool has_probe = td.probe_end > td.probe_begin;
         const Real c2 = pr.c2, kk = pr.k;
-        const int64_t gj = gj0 + (int64_t)tid * P;
+        const int tb = warp * G::CW + lane * P;  // window index of the thread's first point
+        const int64_t gj = gj0 + tb;
+        // registers this thread owns (the others are a warp halo, KH > 0); the
+        // outer halos of the first and last warp have no neighbour and belong to them
+        const int own_lo = (KH > 0 && lane == 0 && warp > 0) ? KH : 0;
+        const int own_hi = (KH > 0 && lane == 31 && warp < NW - 1) ? P - KH : P;
 
         Real* su = stage + x * 2 * W;
         Real* sw = su + W;
         Real u[P], w[P];
-        smem_to_regs<Real, P>(su + tid * P, u);
-        smem_to_regs<Real, P>(sw + tid * P, w);
+        smem_to_regs<Real, P>(su + tb, u);
+        smem_to_regs<Real, P>(sw + tb, w);
+
+        // probes of this tile: staged in shared memory, owners found once
+        const int np = td.probe_end - td.probe_begin;
+        const bool few_probes = np <= kTileProbes;
+        int pq0 = -1, pq1 = -1;
+        if (has_probe && few_probes) {
+            if (tid < np) s_probes[tid] = prm.probes[td.probe_begin + tid];
+            __syncthreads();
+            owned_probes<Real, P>(s_probes, np, wabs, tb, own_lo, own_hi, pq0, pq1);
+        }
 
         // ---- predict: S leapfrog steps of the window
         // special points of this thread (edge / source tiles only)
@@ -236,12 +265,71 @@ __global__ void __launch_bounds__(NT, 2) span_kernel(const __grid_constant__ Spa
 
         // ---- predict: S leapfrog steps of the window
         int buf = 0;
+        bool done_packed = false;
+        if constexpr (PK && KH > 0 && FORM == kIncrement && sizeof(Real) == 4) {
+            if (!slow && !has_probe) {
+                packed_increment_steps<P, NW, KH>(u, w, c2, steps, hx, buf, warp, lane);
+                done_packed = true;
+            }
+        }
+        if (done_packed) {
+        } else if constexpr (KH > 0) {
+            for (int s0 = 0; s0 < steps; s0 += KH) {
+                if (s0 > 0) {
+                    refresh_halos<Real, P, NW, KH>(u, w, hx, buf, warp, lane);
+                    buf ^= 1;
+                }
+                const int s1 = (s0 + KH < steps) ? s0 + KH : steps;
+                for (int s = s0; s < s1; ++s) {
+                    Real lft, rgt;
+                    warp_neighbours<Real, P>(u, lft, rgt, lane);
+                    const int64_t n = n0 + s;
+                    if (has_probe) {
+                        if (few_probes) {
+                            if (pq0 >= 0) record_owned<Real, P>(u, lft, rgt, s_probes[pq0], wabs, tb, n);
+                            if (pq1 >= 0) record_owned<Real, P>(u, lft, rgt, s_probes[pq1], wabs, tb, n);
+                        } else {
+                            record_probes<Real, P>(u, lft, rgt, wabs, tb, own_lo, own_hi, td.probe_begin,
+                                                   td.probe_end, prm.probes, n);
+                        }
+                    }
+                    if (special) {
+                        Real uold_s = Real(0), sval = Real(0);
+                        if (sp.rs >= 0) {
+                            sval = pr.src[(n + 1) * pr.src_stride];
+                            if constexpr (FORM == kIncrement) uold_s = select_reg<Real, P>(u, sp.rs);
+                        }
+                        const Real fa_old = pr.fA ? pr.fA[n] : Real(0);
+                        const Real fa_new = pr.fA ? pr.fA[n + 1] : Real(0);
+                        const Real fb_old = pr.fB ? pr.fB[n] : Real(0);
+                        const Real fb_new = pr.fB ? pr.fB[n + 1] : Real(0);
+                        leap_step<Real, FORM, P>(u, w, lft, rgt, c2, kk);
+                        patch_special<Real, FORM, P>(u, w, sp, uold_s, sval, fa_old, fa_new, fb_old, fb_new);
+                    } else {
+                        leap_step<Real, FORM, P>(u, w, lft, rgt, c2, kk);
+                    }
+                }
+            }
+        } else if (!slow && !has_probe) {
+            // interior tile: halo latency hidden behind the interior updates
+            for (int s = 0; s < steps; ++s) {
+                split_step<Real, FORM, P, NW>(u, w, c2, kk, xch, buf, warp, lane);
+                buf ^= 1;
+            }
+        } else
         for (int s = 0; s < steps; ++s) {
             Real lft, rgt;
             exchange<Real, P, NW>(u, lft, rgt, xch, buf, warp, lane);
             buf ^= 1;
             const int64_t n = n0 + s;
-            if (has_probe) record_probes<Real, P>(u, lft, rgt, wabs, tid, td.probe_begin, td.probe_end, prm.probes, n);
+            if (has_probe) {
+                if (few_probes) {
+                    if (pq0 >= 0) record_owned<Real, P>(u, lft, rgt, s_probes[pq0], wabs, tb, n);
+                    if (pq1 >= 0) record_owned<Real, P>(u, lft, rgt, s_probes[pq1], wabs, tb, n);
+                } else {
+                    record_probes<Real, P>(u, lft, rgt, wabs, tb, 0, P, td.probe_begin, td.probe_end, prm.probes, n);
+                }
+            }
             if (special) {
                 Real uold_s = Real(0), sval = Real(0);
                 if (sp.rs >= 0) {
@@ -260,8 +348,9 @@ __global__ void __launch_bounds__(NT, 2) span_kernel(const __grid_constant__ Spa
         }
 
         // ---- select + update: write the window back, store only the core
-        regs_to_smem<Real, P>(su + tid * P, u);
-        regs_to_smem<Real, P>(sw + tid * P, w);
+        __syncthreads();  // every thread has read its window (KH > 0: windows overlap)
+        owned_to_smem<Real, P, KH>(su + tb, u, own_lo, own_hi);
+        owned_to_smem<Real, P, KH>(sw + tb, w, own_lo, own_hi);
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
@@ -317,32 +406,37 @@ struct Entry {
     size_t smem;
 };
 
-template <typename Real, int FORM, int P, int NT>
+// PK: packed FP32 pairs on interior tiles; MINB: CTAs per SM the register
+// allocation must allow.
+template <typename Real, int FORM, int P, int NT, int KH, int PK = 0, int MINB = 2>
 Entry make_entry()
 {
-    constexpr int W = NT * P;
+    using G = Geom<P, NT, KH>;
     Entry e;
-    e.info = VariantInfo{sizeof(Real) == 8 ? kF64 : kF32, FORM, P, NT};
-    e.fn = reinterpret_cast<const void*>(&span_kernel<Real, FORM, P, NT>);
-    e.smem = sizeof(Real) * (4 * W + 4 * (NT / 32));
+    e.info = VariantInfo{sizeof(Real) == 8 ? kF64 : kF32, FORM, P, NT, KH, G::W};
+    e.fn = reinterpret_cast<const void*>(&span_kernel<Real, FORM, P, NT, KH, PK, MINB>);
+    e.smem = sizeof(Real) * (4 * G::W + G::XCH);
     return e;
 }
 
+// The first entry of each dtype/form is its default (the fastest measured on
+// the c2 workload); the autotuner times them all.
 const Entry* table(int* n)
 {
     static const Entry entries[] = {
-        make_entry<float, kIncrement, 16, 256>(),
-        make_entry<float, kIncrement, 8, 256>(),
-        make_entry<float, kIncrement, 16, 128>(),
-        make_entry<float, kIncrement, 8, 512>(),
-        make_entry<float, kCanonical, 16, 256>(),
-        make_entry<float, kCanonical, 8, 256>(),
-        make_entry<double, kCanonical, 8, 256>(),
-        make_entry<double, kCanonical, 4, 256>(),
-        make_entry<double, kCanonical, 8, 128>(),
-        make_entry<double, kCanonical, 4, 512>(),
-        make_entry<double, kIncrement, 8, 256>(),
-        make_entry<double, kIncrement, 4, 256>(),
+        make_entry<float, kIncrement, 16, 128, 8, 0, 4>(),
+        make_entry<float, kIncrement, 16, 128, 8, 0, 6>(),
+        make_entry<float, kIncrement, 16, 128, 8, 1, 4>(),
+        make_entry<float, kIncrement, 16, 128, 4, 0, 4>(),
+        make_entry<float, kIncrement, 16, 128, 0, 0, 4>(),
+        make_entry<float, kIncrement, 16, 256, 0, 0, 2>(),
+        make_entry<float, kIncrement, 8, 256, 0, 0, 3>(),
+        make_entry<float, kCanonical, 16, 128, 0, 0, 4>(),
+        make_entry<double, kCanonical, 8, 256, 0, 0, 2>(),
+        make_entry<double, kCanonical, 8, 128, 0, 0, 4>(),
+        make_entry<double, kCanonical, 16, 256, 0, 0, 1>(),
+        make_entry<double, kCanonical, 8, 256, 4, 0, 2>(),
+        make_entry<double, kIncrement, 8, 256, 0, 0, 2>(),
     };
     *n = (int)(sizeof(entries) / sizeof(entries[0]));
     return entries;

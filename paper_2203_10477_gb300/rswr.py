@@ -76,6 +76,9 @@ SIGNATURES = {
     "rswr_plan_inject_missing_flag": (_st, [_vp, _i32, _i32]),
     "rswr_plan_autotune": (_st, [_vp, _i64, ctypes.POINTER(_i32), _vp]),
     "rswr_plan_set_kernel_events": (_st, [_vp, _vp, _vp]),
+    "rswr_plan_set_graph": (_st, [_vp, _i32]),
+    "rswr_batch_set_graph": (_st, [_vp, _i32]),
+    "rswr_batch_autotune": (_st, [_vp, _i64, ctypes.POINTER(_i32), _vp]),
     "rswr_batch_set_kernel_events": (_st, [_vp, _vp, _vp]),
     "rswr_plan_check": (_st, [_vp, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "rswr_run": (_st, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
@@ -217,6 +220,9 @@ class Plan:
     def set_wait_limit(self, seconds: float):
         check(lib().rswr_plan_set_wait_limit(self.h, seconds))
 
+    def set_graph(self, enable: bool):
+        check(lib().rswr_plan_set_graph(self.h, int(enable)))
+
     def inject_missing_flag(self, tile: int, span: int):
         check(lib().rswr_plan_inject_missing_flag(self.h, tile, span))
 
@@ -346,6 +352,14 @@ class Batch:
 
     def set_wait_limit(self, seconds: float):
         check(lib().rswr_batch_set_wait_limit(self.h, seconds))
+
+    def set_graph(self, enable: bool):
+        check(lib().rswr_batch_set_graph(self.h, int(enable)))
+
+    def autotune(self, probe_steps: int, stream=None) -> int:
+        v = _i32()
+        check(lib().rswr_batch_autotune(self.h, probe_steps, ctypes.byref(v), _stream(stream)))
+        return v.value
 
     def set_kernel_events(self, start=None, stop=None):
         h = lambda ev: None if ev is None else ev.cuda_event

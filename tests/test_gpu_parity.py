@@ -267,6 +267,26 @@ def test_adjoint_grad_fA_fp64_bitwise(R, oracle_mod, jr):
     assert_bitwise(host(res["grad_fA"]), ref["dg"], "grad_fA")
 
 
+@pytest.mark.parametrize("T", [300, 2000])
+def test_adjoint_grad_fA_fp32_bitwise_vs_fp32_sweep(R, oracle_mod, T):
+    """The FP32 adjoint is exactly the FP32 increment-form leapfrog with the
+    adjoint source (oracle emulation), bit for bit."""
+    nx, N, ov, jr = 3001, 4, 64, 1200
+    a = 1.3
+    dt = 0.9 / (nx - 1) / a
+    w = inputs.rng(6).standard_normal(T + 1)
+    plan = R.Plan(0.0, 1.0, a, nx, dt, N, ov, dtype=F32)
+    got = host(plan.adjoint(None, None, T, jr, w)["grad_fA"])
+    w32 = w.astype(np.float32)
+    src = np.concatenate([[0.0], w32[::-1].astype(np.float64)])
+    zz = np.zeros(T + 2)
+    lam = oracle_mod.leapfrog(nx, T + 1, a, dt, zz, zz, form=1, prec="f32", rec_j=[1], src_j=jr, src=src)
+    c2f = lam["coeffs"].c2f
+    dg = np.array([np.float32(c2f) * np.float32(lam["rec"][0][T - n]) for n in range(T)], dtype=np.float32)
+    assert_bitwise(got[:T], dg, "FP32 adjoint")
+    assert got[T] == 0.0
+
+
 def test_adjoint_grad_fA_fp32_close(R, oracle_mod):
     nx, N, ov, T = 3001, 4, 64, 2000
     a = 1.3
@@ -416,3 +436,130 @@ def test_missing_flag_times_out_and_context_survives(R, oracle_mod):
     plan.check()
     ref = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, np.zeros(T + 1), nx_run=oracle_mod.causal_extent(T, nx))
     assert_bitwise(host(out["u"])[: len(ref["u"])], ref["u"], "after timeout")
+
+
+# ----------------------------------------------------------------------------
+# CUDA graphs, autotuner
+# ----------------------------------------------------------------------------
+
+def test_graph_replay_and_direct_launch_agree(R, oracle_mod):
+    nx, N, ov, T = 40009, 6, 48, 321
+    dt = 0.9 / (nx - 1)
+    fA = torch.tensor(inputs.gaussian_pulse(T, dt, sigma_steps=12), device="cuda", dtype=torch.float64)
+    q0 = torch.tensor(inputs.smooth_random_state(nx, seed=2), device="cuda", dtype=torch.float64)
+    out = (torch.empty(nx, dtype=torch.float64, device="cuda"), torch.empty(nx, dtype=torch.float64, device="cuda"))
+    plan = R.Plan(0.0, 1.0, 1.0, nx, dt, N, ov, dtype=F64)
+    ref = oracle_mod.leapfrog(nx, T, 1.0, dt, host(fA), np.zeros(T + 1), q0=host(q0))
+    for mode in (0, 1):
+        plan.set_mode(mode)
+        for graph in (True, True, False, True):  # capture, replay, direct, capture again
+            plan.set_graph(graph)
+            out[0].fill_(7.0)
+            plan.run(fA, None, T, q0=q0, out=out)
+            plan.check()
+            assert_bitwise(host(out[0]), ref["u"], f"mode {mode} graph {graph}")
+
+
+def test_batch_autotune_then_exact(R, oracle_mod):
+    r = inputs.rng(31)
+    T = 257
+    probs = []
+    for i in range(9):
+        nx = int(r.integers(3000, 60000))
+        dt = inputs.dt_for_cfl(nx, 1.0, 0.8)
+        probs.append(inputs.Problem(nx, 1.0, dt, T, max(1, nx // 2048), 32, inputs.sine(T, dt, 3.0 + i), np.zeros(T + 1)))
+    b = R.Batch(probs, dtype=F32)
+    v = b.autotune(48)
+    info = b.info()
+    assert info["variant"] == v and 1 <= info["span_steps"] <= 16
+    out = b.run(np.concatenate([p.fA for p in probs]), None, T)
+    b.check()
+    u = host(out["u"])
+    for i, p in enumerate(probs):
+        ref = oracle_mod.leapfrog(p.nx, T, p.a, p.dt, p.fA, p.fB, form=1, prec="f32")
+        assert_bitwise(u[b.offsets[i]:b.offsets[i + 1]], ref["u"], f"problem {i}")
+
+
+# ----------------------------------------------------------------------------
+# full-size workloads (sampled / causal-prefix parity)
+# ----------------------------------------------------------------------------
+
+def test_c2_full_size_both_precisions(R, oracle_mod):
+    """nx = 2^24, N = 1024, overlap 64, CFL 0.9, 10^4 steps: the bench workload."""
+    p = inputs.c2()
+    n = oracle_mod.causal_extent(p.T, p.nx)
+    ref64 = oracle_mod.leapfrog(p.nx, p.T, p.a, p.dt, p.fA, p.fB, rec_j=[5000], nx_run=n)
+    ref32 = oracle_mod.leapfrog(p.nx, p.T, p.a, p.dt, p.fA, p.fB, rec_j=[5000], nx_run=n, form=1, prec="f32")
+    for dtype, ref in ((F64, ref64), (F32, ref32)):
+        plan = R.Plan.from_problem(p, dtype=dtype)
+        out = plan.run(p.fA, p.fB, p.T, j_r=5000)
+        plan.check()
+        u = host(out["u"])
+        assert_bitwise(u[:n], ref["u"], f"c2 dtype {dtype} causal prefix")
+        assert np.all(u[n:] == 0.0)
+        assert_bitwise(host(out["recv"]), ref["rec"][0], "c2 receiver")
+        if dtype == F32:
+            err = np.abs(u[:n].astype(np.float64) - ref64["u"]).max() / np.abs(ref64["u"]).max()
+            assert err <= 1e-5, err
+
+
+def test_c3_full_size_batch_sampled(R, oracle_mod):
+    """4096 independent problems (nx in [2^10, 2^18], a in [0.5, 2], CFL 0.8,
+    4096 steps, N_p = ceil(nx/2048), overlap 32), one persistent launch; 24
+    sampled problems against the oracle on their causal prefix, every problem
+    exactly 0 beyond it."""
+    probs = inputs.c3_problems()
+    T = probs[0].T
+    b = R.Batch(probs, dtype=F32)
+    fA = np.concatenate([p.fA for p in probs])
+    out = b.run(fA, None, T)
+    b.check()
+    u = host(out["u"])
+    off = b.offsets
+    n_of = lambda p: oracle_mod.causal_extent(T, p.nx)
+    for i, p in enumerate(probs):
+        assert np.all(u[off[i] + n_of(p):off[i + 1]] == 0.0), i
+    for i in inputs.rng(5).choice(len(probs), 24, replace=False):
+        p = probs[i]
+        n = n_of(p)
+        ref = oracle_mod.leapfrog(p.nx, T, p.a, p.dt, p.fA, p.fB, form=1, prec="f32", nx_run=n)
+        assert_bitwise(u[off[i]:off[i] + n], ref["u"], f"c3 problem {i}")
+
+
+def test_c5_full_size(R, oracle_mod):
+    """nx = 2^28 FP32, N = 8192, overlap 64, 2^15 steps (causal-prefix parity),
+    then 512 uneven problems (nx in [2^12, 2^20]) with boundary-waveform
+    gradients of a receiver misfit (two sampled problems against the oracle)."""
+    p = inputs.c5_big()
+    plan = R.Plan.from_problem(p, dtype=F32)
+    out = plan.run(p.fA, p.fB, p.T, j_r=20000)
+    plan.check()
+    n = oracle_mod.causal_extent(p.T, p.nx)
+    u = out["u"]
+    assert float(u[n:].abs().max()) == 0.0
+    ref = oracle_mod.leapfrog(p.nx, p.T, p.a, p.dt, p.fA, p.fB, rec_j=[20000], nx_run=n, form=1, prec="f32")
+    assert_bitwise(host(u[:n]), ref["u"], "c5 causal prefix")
+    assert_bitwise(host(out["recv"]), ref["rec"][0], "c5 receiver")
+    del out, u, plan
+    torch.cuda.empty_cache()
+
+    probs = inputs.c5_uneven()
+    T = probs[0].T
+    jr = [q.meta["j_r"] for q in probs]
+    b = R.Batch(probs, dtype=F32)
+    fA = np.concatenate([q.fA for q in probs])
+    # smooth cotangents (like a misfit residual of smooth traces) and white noise
+    smooth = np.stack([inputs.lowpass_noise(T, seed=1000 + i) for i in range(len(probs))])
+    rough = inputs.rng(77).standard_normal((len(probs), T + 1))
+    for w, tol in ((smooth, 5e-4), (rough, 5e-4)):
+        g = b.adjoint(fA, None, T, jr, w)
+        b.check()
+        gf = host(g["grad_fA"])
+        assert np.all(np.isfinite(gf))
+        for i in (3, 200):
+            q = probs[i]
+            ref = oracle_mod.adjoint(q.nx, T, q.a, q.dt, q.fA, q.fB, jr[i], w[i],
+                                     nx_run=oracle_mod.causal_extent(T, q.nx))
+            err = np.linalg.norm(gf[i].astype(np.float64) - ref["dg"]) / np.linalg.norm(ref["dg"])
+            print(f"c5 problem {i} FP32 grad_fA rel. 2-norm error {err:.2e} (tolerance {tol:g})")
+            assert err <= tol, (i, err)

@@ -386,3 +386,22 @@ def test_adjoint_causal_truncation_is_exact(oracle_mod):
     cut = oracle_mod.adjoint(nx, T, 1.3, dt, g, z, jr, w, nx_run=oracle_mod.causal_extent(T, nx))
     assert np.array_equal(full["dg"], cut["dg"])
     assert full["dc2"] == cut["dc2"]
+
+
+def test_source_driven_leapfrog_is_the_adjoint_sweep(oracle_mod):
+    """The adjoint variables in reversed time are the leapfrog from rest with
+    zero Dirichlet data and the source wbar[T+1-m] at j_r: its samples at j = 1
+    times c2 are dL/dfA, equal to the oracle's discrete adjoint bit for bit."""
+    nx, T, jr = 301, 420, 120
+    dt = 0.9 / (nx - 1) / 1.3
+    g = inputs.lowpass_noise(T, seed=21)
+    z = np.zeros(T + 1)
+    w = inputs.rng(3).standard_normal(T + 1)
+    adj = oracle_mod.adjoint(nx, T, 1.3, dt, g, z, jr, w)
+    src = np.concatenate([[0.0], w[::-1]])  # level m of the reversed run gets wbar[T+1-m]
+    zz = np.zeros(T + 2)
+    lam = oracle_mod.leapfrog(nx, T + 1, 1.3, dt, zz, zz, rec_j=[1], src_j=jr, src=src)
+    c2 = adj["coeffs"].c2
+    dg = np.array([c2 * lam["rec"][0][T - n] for n in range(T + 1)])
+    assert np.array_equal(dg[:T], adj["dg"][:T])
+    assert dg[T] == 0.0 and adj["dg"][T] == 0.0
