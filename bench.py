@@ -301,6 +301,101 @@ def profile_case(which: str, variant=None) -> None:
     print(json.dumps({"profile_case": which, "nx": p.nx, "T": p.T, "info": plan.info()}))
 
 
+# ----------------------------------------------------------------------------
+# extra measurements: batched (c3), adjoint (c4), large grid (c5)
+# ----------------------------------------------------------------------------
+
+def _time(torch, fn, reps):
+    stream = torch.cuda.current_stream()
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms
+
+
+def bench_batched(torch, rank, world, dist, dev):
+    """4096 independent problems (nx in [2^10, 2^18], CFL 0.8, 4096 steps,
+    overlap 32), FP32, one persistent launch per run; problems sharded across
+    ranks by size."""
+    from paper_2203_10477_gb300 import rswr
+    from paper_2203_10477_gb300.shard import max_over_ranks, shard_problems, sum_over_ranks
+
+    probs = inputs.c3_problems()
+    T = probs[0].T
+    mine = [probs[i] for i in shard_problems([p.nx for p in probs], rank, world)]
+    b = rswr.Batch(mine, dtype=rswr.F32, device=dev)
+    b.autotune(64)
+    fA = torch.as_tensor(np.concatenate([p.fA for p in mine]), device=dev).to(torch.float32)
+    n = int(b.offsets[-1])
+    out = (torch.empty(n, dtype=torch.float32, device=dev), torch.empty(n, dtype=torch.float32, device=dev))
+    run = lambda: b.run(fA, None, T, out=out)
+    run()
+    ms = _time(torch, run, 2)
+    b.check()
+    lups = float(sum((p.nx - 2) * T for p in mine))
+    t = max_over_ranks([sum(ms) / len(ms) / 1e3], dist, dev)[0]
+    tot = sum_over_ranks([lups], dist, dev)[0]
+    info = b.info()
+    return {"workload": "4096 problems, nx U[2^10,2^18], a U[0.5,2], CFL 0.8, 4096 steps, overlap 32, FP32",
+            "value": tot / t / 1e9, "unit": UNIT, "ms_per_run": 1e3 * t, "lups_per_run": tot,
+            "variant": info["variant"], "span_steps": info["span_steps"], "mode": info["mode"],
+            "sharding": f"{world} rank(s), whole problems per rank"}
+
+
+def bench_adjoint(torch, dev):
+    """c4 gradients (nx = 2^20, a = 1.3, CFL 0.9, 8192 steps, N = 256, overlap
+    64; receiver j_r = 4000): dL/dfA and dL/da with checkpoints and in-kernel
+    recompute.  GLUP/s counts the forward problem's updates per gradient."""
+    from paper_2203_10477_gb300 import rswr
+
+    p = inputs.c4(j_r=4000)
+    res = {}
+    w = torch.as_tensor(inputs.lowpass_noise(p.T, seed=4), device=dev)
+    for name, dtype in (("f64", rswr.F64), ("f32", rswr.F32)):
+        plan = rswr.Plan.from_problem(p, dtype=dtype, device=dev)
+        td = torch.float64 if dtype == rswr.F64 else torch.float32
+        fA = torch.as_tensor(p.fA, device=dev).to(td)
+        wt = w.to(td)
+        full = lambda: plan.adjoint(fA, None, p.T, 4000, wt, want_a=True)
+        gonly = lambda: plan.adjoint(fA, None, p.T, 4000, wt, want_a=False)
+        full()
+        gonly()
+        ms_full = _time(torch, full, 2)
+        ms_g = _time(torch, gonly, 2)
+        plan.check()
+        lups = (p.nx - 2) * p.T
+        res[name] = {"grad_fA_and_a": {"value": lups / (min(ms_full) / 1e3) / 1e9, "ms": min(ms_full)},
+                     "grad_fA_only": {"value": lups / (min(ms_g) / 1e3) / 1e9, "ms": min(ms_g)}}
+    res["unit"] = UNIT
+    res["workload"] = "c4: nx=2^20, a=1.3, CFL 0.9, 8192 steps, N=256, overlap 64, receiver j_r=4000"
+    return res
+
+
+def bench_large(torch, dev):
+    """c5 grid: nx = 2^28 FP32, N = 8192, overlap 64, 2^15 steps (8.8e12 updates)."""
+    from paper_2203_10477_gb300 import rswr
+
+    p = inputs.c5_big()
+    plan = rswr.Plan.from_problem(p, dtype=rswr.F32, device=dev)
+    plan.autotune(64)
+    fA = torch.as_tensor(p.fA, device=dev).to(torch.float32)
+    out = (torch.empty(p.nx, dtype=torch.float32, device=dev), torch.empty(p.nx, dtype=torch.float32, device=dev))
+    run = lambda: plan.run(fA, None, p.T, out=out)
+    run()
+    ms = _time(torch, run, 1)
+    plan.check()
+    lups = (p.nx - 2) * p.T
+    info = plan.info()
+    del out
+    return {"workload": "c5: nx=2^28 FP32, N=8192, overlap 64, 2^15 steps", "value": lups / (ms[0] / 1e3) / 1e9,
+            "unit": UNIT, "ms_per_run": ms[0], "variant": info["variant"], "span_steps": info["span_steps"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -309,6 +404,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mono", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched / adjoint / large-grid measurements")
     ap.add_argument("--profile-case", choices=["f64", "f32"], default=None,
                     help="run the small profiling case (nx=2^22, 320 steps) twice and exit (for ncu)")
     ap.add_argument("--variant", type=int, default=None, help="kernel variant of the profiling case")
@@ -368,12 +464,9 @@ def main():
         dist.barrier()
     clk = clocks.stop()
 
-    t64 = sum(run64) / 1e3
-    t32 = sum(run32) / 1e3
-    if dist:
-        tt = torch.tensor([t64, t32], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t64, t32 = tt.tolist()
+    from paper_2203_10477_gb300.shard import max_over_ranks
+
+    t64, t32 = max_over_ranks([sum(run64) / 1e3, sum(run32) / 1e3], dist, dev)
     n = world
     value64 = n * lups * args.steps / t64 / 1e9
     value32 = n * lups * args.steps / t32 / 1e9
@@ -451,6 +544,14 @@ def main():
                                "313 spans) + probe_final_kernel; FP64 and FP32 runs",
         "clocks": clk,
     }
+    if not args.no_extras:
+        del b64, b32
+        torch.cuda.empty_cache()
+        line["batched"] = bench_batched(torch, rank, world, dist, dev)
+        torch.cuda.empty_cache()
+        line["adjoint"] = bench_adjoint(torch, dev)
+        torch.cuda.empty_cache()
+        line["large_grid"] = bench_large(torch, dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
     if rank == 0:
