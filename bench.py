@@ -396,6 +396,27 @@ def bench_large(torch, dev):
             "unit": UNIT, "ms_per_run": ms[0], "variant": info["variant"], "span_steps": info["span_steps"]}
 
 
+def bench_paper_literal(torch, dev, T=2000):
+    """The paper-literal RSWR (data-chosen spans, flux-exchange update) on the
+    c2 grid (nx = 2^24, N = 1024, overlap 64, CFL 0.9) for 2000 steps."""
+    from paper_2203_10477_gb300 import rswr
+
+    p = inputs.c2(T=T)
+    res = {"workload": "c2 grid, 2000 steps, paper-literal select/update", "unit": UNIT}
+    for name, dtype in (("f64", rswr.F64), ("f32", rswr.F32)):
+        plan = rswr.Plan.from_problem(p, dtype=dtype, device=dev)
+        td = torch.float64 if dtype == rswr.F64 else torch.float32
+        fA = torch.as_tensor(p.fA, device=dev).to(td)
+        out = (torch.empty(p.nx, dtype=td, device=dev), torch.empty(p.nx, dtype=td, device=dev))
+        plan.run_paper(fA, None, 64, out=out)
+        t0 = time.perf_counter()
+        r = plan.run_paper(fA, None, p.T, out=out)
+        secs = time.perf_counter() - t0
+        res[name] = {"value": (p.nx - 2) * p.T / secs / 1e9, "seconds": secs, "spans": int(len(r["spans"])),
+                     "mean_span": float(np.mean(r["spans"]))}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -552,6 +573,8 @@ def main():
         line["adjoint"] = bench_adjoint(torch, dev)
         torch.cuda.empty_cache()
         line["large_grid"] = bench_large(torch, dev)
+        torch.cuda.empty_cache()
+        line["paper_literal"] = bench_paper_literal(torch, dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
     if rank == 0:

@@ -193,6 +193,24 @@ rswr_status rswr_run_host(rswr_plan_t plan, const void* fA, const void* fB, int6
                           const void* q1, void* out0, void* out1, void* traces, int64_t j_r, void* recv,
                           void* stream);
 
+/* RSWR exactly as the paper states it (Sec. 2.3-2.6, Sec. 3), with the span
+ * chosen from the data every time: each interface predicts both neighbours
+ * over the predictive span tau with a zero input-flux guess; the pair's span
+ * is the largest number of leading steps over which the two predictions agree
+ * exactly at some overlap point; the global span is the minimum over pairs,
+ * capped by the Waveform Time Span Theorem (steps < (overlap - 1)/(2c)); each
+ * subdomain is then solved again over that span with the neighbour's
+ * predicted output flux as Neumann data, u = p_i on Omega_i minus the windows
+ * left of it, and the next predictive span is ceil(1.1 * span) (beta = 0.1;
+ * first span tau = overlap).  Equal to the monolithic solve up to rounding
+ * (the flux round trip g = (u+ - u-)/(2dx), ghost = u + 2dx g).
+ * Same arguments as rswr_run (no traces or receiver); spans (host, capacity
+ * spans_cap, may be NULL) receives the selected spans, *nspans their count.
+ * Synchronous (the host reads every selected span). */
+rswr_status rswr_run_paper(rswr_plan_t plan, const void* fA, const void* fB, int64_t T, const void* q0,
+                           const void* q1, void* out0, void* out1, int64_t* spans, int64_t spans_cap,
+                           int64_t* nspans, void* stream);
+
 /* The monolithic comparator: the same arguments and results as rswr_run,
  * computed by one whole-grid leapfrog step per launch (no decomposition, the
  * paper's true solution of Sec. 2.1).  Bit-identical to rswr_run. */

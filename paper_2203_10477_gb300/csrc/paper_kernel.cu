@@ -1,0 +1,232 @@
+// paper_kernel.cu -- RSWR exactly as the paper states it (arXiv 2203.10477,
+// Sec. 2.3-2.6, Sec. 3), on the GPU: adaptive spans chosen from the data.
+//
+// One span:
+//   rswr_iface_kernel  (one CTA per interface i | i+1, Sec. 2.3-2.4): predicts
+//       subdomains i and i+1 on the part of their windows that can reach the
+//       overlap within the predictive span tau (zero input-flux guess at
+//       their input boundaries), records the predicted output flux waveforms
+//       both neighbours need for the update (Sec. 2.5), compares the two
+//       predictions on the overlap and takes, as the pair's maximum span,
+//       the largest number of leading steps over which they agree exactly at
+//       some overlap point; the global span is the minimum over pairs (Sec. 3,
+//       atomicMin).
+//   host: caps the span by the Waveform Time Span Theorem (Sec. 2.4).
+//   rswr_resolve_kernel (tiles of each subdomain's part of the combined
+//       solution, Sec. 2.5): solves the subdomain again over the span with
+//       its input flux set to the neighbour's predicted output flux
+//       (Neumann ghost u_{L-1} = u_{L+1} - 2 dx g, u_{R+1} = u_{R-1} + 2 dx g)
+//       and writes the points of Omega_i not covered by a window further left.
+//   host: next predictive span = ceil((1 + beta) * span) (Sec. 2.6).
+// Simple kernels: one window in shared memory per CTA, a block barrier per
+// step.  This is the fidelity path; the fast path is the span kernel.
+
+#include "rswr_internal.h"
+
+namespace rswr {
+
+namespace {
+
+template <typename Real>
+__device__ __forceinline__ void upd(int form, Real c2, Real k, Real uL, Real uC, Real uR, Real w, Real& un, Real& wn)
+{
+    if (form == kCanonical) {
+        un = rfma(c2, radd(uL, uR), rfma(k, uC, -w));
+        wn = uC;
+    } else {
+        const Real v = rfma(c2, radd(rsub(uL, uC), rsub(uR, uC)), w);
+        un = radd(uC, v);
+        wn = v;
+    }
+}
+
+template <typename Real>
+__device__ __forceinline__ Real dir_w(int form, Real f_old, Real f_new)
+{
+    return form == kCanonical ? f_old : rsub(f_new, f_old);
+}
+
+__device__ __forceinline__ int64_t win_l(int64_t i, int64_t nx, int64_t N, int64_t el)
+{
+    const int64_t b0 = i * nx / N;
+    return b0 - el < 0 ? 0 : b0 - el;
+}
+
+__device__ __forceinline__ int64_t win_r(int64_t i, int64_t nx, int64_t N, int64_t er)
+{
+    const int64_t b1 = (i + 1) * nx / N;
+    return b1 - 1 + er > nx - 1 ? nx - 1 : b1 - 1 + er;
+}
+
+// One step of a window [lo, hi] of subdomain `sub` held in shared memory.
+// Edge rules: Dirichlet at the grid ends; at the subdomain's input boundaries
+// either the zero-flux guess (g == nullptr) or the Neumann ghost from g[s];
+// a cut that is not a subdomain boundary gets the mirror (its points are
+// outside the part of the window that is kept).
+template <typename Real>
+__device__ void window_step(int form, Real c2, Real k, Real two_dx, int64_t nx, int64_t lo, int64_t hi, int64_t Lsub,
+                            int64_t Rsub, const Real* gL, const Real* gR, int s, const Real* fA, const Real* fB,
+                            int64_t n, const Real* u, const Real* w, Real* un, Real* wn)
+{
+    for (int64_t j = lo + threadIdx.x; j <= hi; j += blockDim.x) {
+        const int64_t o = j - lo;
+        if (j == 0) {
+            const Real a0 = fA ? fA[n] : Real(0), a1 = fA ? fA[n + 1] : Real(0);
+            un[o] = a1;
+            wn[o] = dir_w<Real>(form, a0, a1);
+            continue;
+        }
+        if (j == nx - 1) {
+            const Real b0 = fB ? fB[n] : Real(0), b1 = fB ? fB[n + 1] : Real(0);
+            un[o] = b1;
+            wn[o] = dir_w<Real>(form, b0, b1);
+            continue;
+        }
+        Real uL, uR;
+        if (j == lo) {
+            if (j == Lsub && gL) uL = rsub(u[o + 1], rmul(two_dx, gL[s]));
+            else uL = u[o + 1];
+        } else {
+            uL = u[o - 1];
+        }
+        if (j == hi) {
+            if (j == Rsub && gR) uR = radd(u[o - 1], rmul(two_dx, gR[s]));
+            else uR = u[o - 1];
+        } else {
+            uR = u[o + 1];
+        }
+        upd<Real>(form, c2, k, uL, u[o], uR, w[o], un[o], wn[o]);
+    }
+}
+
+template <typename Real>
+__global__ void rswr_iface_kernel(const __grid_constant__ PaperParams<Real> p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t i = blockIdx.x;  // interface between subdomains i and i+1
+    const int64_t nx = p.nx, N = p.N;
+    const int64_t Li = win_l(i, nx, N, p.el), Ri = win_r(i, nx, N, p.er);
+    const int64_t Ln = win_l(i + 1, nx, N, p.el), Rn = win_r(i + 1, nx, N, p.er);
+    const int steps = p.steps;
+    const int64_t a0 = Ln - steps > Li ? Ln - steps : Li;  // prediction of i: [a0, Ri]
+    const int64_t b1 = Ri + steps < Rn ? Ri + steps : Rn;  // prediction of i+1: [Ln, b1]
+    const int64_t na = Ri - a0 + 1, nb = b1 - Ln + 1, nov = Ri - Ln + 1;
+    Real* s = reinterpret_cast<Real*>(smem_raw);
+    Real* ua = s;
+    Real* wa = ua + na;
+    Real* ua2 = wa + na;
+    Real* wa2 = ua2 + na;
+    Real* ub = wa2 + na;
+    Real* wb = ub + nb;
+    Real* ub2 = wb + nb;
+    Real* wb2 = ub2 + nb;
+    int* agree = reinterpret_cast<int*>(wb2 + nb);  // [nov]: leading steps of exact agreement, -1 = stopped
+    for (int64_t o = threadIdx.x; o < na; o += blockDim.x) {
+        ua[o] = p.u[a0 + o];
+        wa[o] = p.w[a0 + o];
+    }
+    for (int64_t o = threadIdx.x; o < nb; o += blockDim.x) {
+        ub[o] = p.u[Ln + o];
+        wb[o] = p.w[Ln + o];
+    }
+    for (int64_t o = threadIdx.x; o < nov; o += blockDim.x) agree[o] = 0;
+    __syncthreads();
+    for (int st = 0; st < steps; ++st) {
+        const int64_t n = p.n0 + st;
+        // output flux waveforms at level n: subdomain i at Ln (for i+1), i+1 at Ri (for i)
+        if (threadIdx.x == 0) {
+            p.gL[(i + 1) * p.tau_stride + st] = rdiv(rsub(ua[Ln + 1 - a0], ua[Ln - 1 - a0]), p.two_dx);
+            p.gR[i * p.tau_stride + st] = rdiv(rsub(ub[Ri + 1 - Ln], ub[Ri - 1 - Ln]), p.two_dx);
+        }
+        window_step<Real>(p.form, p.c2, p.k, p.two_dx, nx, a0, Ri, Li, Ri, nullptr, nullptr, st, p.fA, p.fB, n, ua, wa,
+                          ua2, wa2);
+        window_step<Real>(p.form, p.c2, p.k, p.two_dx, nx, Ln, b1, Ln, Rn, nullptr, nullptr, st, p.fA, p.fB, n, ub, wb,
+                          ub2, wb2);
+        __syncthreads();
+        for (int64_t o = threadIdx.x; o < nov; o += blockDim.x) {
+            if (agree[o] >= 0) {
+                if (ua2[Ln + o - a0] == ub2[o]) agree[o] = st + 1;
+                else agree[o] = -(agree[o] + 1);  // stop, remembering the count
+            }
+        }
+        Real* t;
+        t = ua; ua = ua2; ua2 = t;
+        t = wa; wa = wa2; wa2 = t;
+        t = ub; ub = ub2; ub2 = t;
+        t = wb; wb = wb2; wb2 = t;
+        __syncthreads();
+    }
+    // the pair's maximum span: largest agreement over the overlap
+    __shared__ int best;
+    if (threadIdx.x == 0) best = 0;
+    __syncthreads();
+    for (int64_t o = threadIdx.x; o < nov; o += blockDim.x) {
+        const int a = agree[o] >= 0 ? agree[o] : -agree[o] - 1;
+        atomicMax(&best, a);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMin(p.span_min, best);
+}
+
+template <typename Real>
+__global__ void rswr_resolve_kernel(const __grid_constant__ PaperParams<Real> p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t t = blockIdx.x;
+    const int64_t i = p.tile_sub[t], c0 = p.tile_lo[t], c1 = p.tile_hi[t];  // owned [c0, c1) of subdomain i
+    const int64_t nx = p.nx, N = p.N;
+    const int64_t Li = win_l(i, nx, N, p.el), Ri = win_r(i, nx, N, p.er);
+    const int span = p.steps;
+    const int64_t lo = c0 - span > Li ? c0 - span : Li;
+    const int64_t hi = c1 - 1 + span < Ri ? c1 - 1 + span : Ri;
+    const int64_t nw = hi - lo + 1;
+    Real* s = reinterpret_cast<Real*>(smem_raw);
+    Real* u = s;
+    Real* w = u + nw;
+    Real* u2 = w + nw;
+    Real* w2 = u2 + nw;
+    for (int64_t o = threadIdx.x; o < nw; o += blockDim.x) {
+        u[o] = p.u[lo + o];
+        w[o] = p.w[lo + o];
+    }
+    __syncthreads();
+    const Real* gL = (i > 0 && Li > 0) ? p.gL + i * p.tau_stride : nullptr;
+    const Real* gR = (i + 1 < N && Ri < nx - 1) ? p.gR + i * p.tau_stride : nullptr;
+    for (int st = 0; st < span; ++st) {
+        window_step<Real>(p.form, p.c2, p.k, p.two_dx, nx, lo, hi, Li, Ri, gL, gR, st, p.fA, p.fB, p.n0 + st, u, w,
+                          u2, w2);
+        __syncthreads();
+        Real* tt;
+        tt = u; u = u2; u2 = tt;
+        tt = w; w = w2; w2 = tt;
+    }
+    for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
+        p.uo[j] = u[j - lo];
+        p.wo[j] = w[j - lo];
+    }
+}
+
+}  // namespace
+
+cudaError_t paper_iface_launch(int dtype, const void* params, int n_iface, size_t smem, cudaStream_t s)
+{
+    if (n_iface <= 0) return cudaSuccess;
+    void* args[] = {const_cast<void*>(params)};
+    const void* fn = dtype == kF64 ? reinterpret_cast<const void*>(&rswr_iface_kernel<double>)
+                                   : reinterpret_cast<const void*>(&rswr_iface_kernel<float>);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernel(fn, dim3(n_iface), dim3(256), args, smem, s);
+}
+
+cudaError_t paper_resolve_launch(int dtype, const void* params, int ntiles, size_t smem, cudaStream_t s)
+{
+    void* args[] = {const_cast<void*>(params)};
+    const void* fn = dtype == kF64 ? reinterpret_cast<const void*>(&rswr_resolve_kernel<double>)
+                                   : reinterpret_cast<const void*>(&rswr_resolve_kernel<float>);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernel(fn, dim3(ntiles), dim3(256), args, smem, s);
+}
+
+}  // namespace rswr

@@ -1241,6 +1241,134 @@ rswr_status autotune_engine(Engine* e, int64_t probe_steps, int32_t* variant, cu
 
 }  // namespace
 
+namespace {
+
+// ---- the paper-literal span loop (see paper_kernel.cu) --------------------
+template <typename Real>
+rswr_status run_paper(Engine* e, const Real* fA, const Real* fB, int64_t T, const Real* q0, const Real* q1, Real* out0,
+                      Real* out1, int64_t* spans, int64_t spans_cap, int64_t* nspans, double beta, cudaStream_t s)
+{
+    const ProbHost& ph = e->probs[0];
+    const int64_t nx = ph.nx, N = ph.n_sub, ov = ph.ov, el = (ov + 1) / 2, er = ov / 2;
+    const size_t es = sizeof(Real);
+    int64_t cap = (int64_t)std::ceil((double)(ov - 1) / (2.0 * ph.c)) - 1;
+    if (cap < 1) cap = 1;
+    int64_t tau = ov;
+    const int64_t tau_max = (int64_t)std::ceil((1.0 + beta) * (double)std::max(tau, cap)) + 1;
+    auto wl = [&](int64_t i) { return std::max<int64_t>(i * nx / N - el, 0); };
+    auto wr = [&](int64_t i) { return std::min<int64_t>((i + 1) * nx / N - 1 + er, nx - 1); };
+    // re-solve tiles: each subdomain's part of the combined solution, in chunks
+    constexpr int64_t CH = 1024;
+    std::vector<int64_t> tsub, tlo, thi;
+    for (int64_t i = 0; i < N; ++i) {
+        const int64_t from = (i == 0) ? wl(0) : wr(i - 1) + 1;
+        for (int64_t c = from; c <= wr(i); c += CH) {
+            tsub.push_back(i);
+            tlo.push_back(c);
+            thi.push_back(std::min(c + CH, wr(i) + 1));
+        }
+    }
+    const int64_t nt = (int64_t)tsub.size();
+    // workspace: two plain state pairs, flux waveforms, tiles, span word
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t b_state = up(es * nx);
+    const size_t b_g = up(es * N * tau_max);
+    const size_t need = 4 * b_state + 2 * b_g + 3 * up(sizeof(int64_t) * nt) + 256;
+    if (need > e->adj_mem_cap) {
+        RSWR_CUDA(cudaStreamSynchronize(s));
+        cudaFree(e->adj_mem);
+        e->adj_mem = nullptr;
+        e->adj_mem_cap = 0;
+        if (cudaMalloc(&e->adj_mem, need) != cudaSuccess) return fail(RSWR_ENOMEM, "paper-literal workspace");
+        e->adj_mem_cap = need;
+    }
+    char* m = static_cast<char*>(e->adj_mem);
+    Real* X0 = reinterpret_cast<Real*>(m);
+    Real* X1 = reinterpret_cast<Real*>(m + b_state);
+    Real* Y0 = reinterpret_cast<Real*>(m + 2 * b_state);
+    Real* Y1 = reinterpret_cast<Real*>(m + 3 * b_state);
+    Real* gL = reinterpret_cast<Real*>(m + 4 * b_state);
+    Real* gR = reinterpret_cast<Real*>(m + 4 * b_state + b_g);
+    int64_t* d_sub = reinterpret_cast<int64_t*>(m + 4 * b_state + 2 * b_g);
+    int64_t* d_lo = d_sub + up(sizeof(int64_t) * nt) / sizeof(int64_t);
+    int64_t* d_hi = d_lo + up(sizeof(int64_t) * nt) / sizeof(int64_t);
+    int* d_span = reinterpret_cast<int*>(d_hi + up(sizeof(int64_t) * nt) / sizeof(int64_t));
+    RSWR_CUDA(cudaMemcpyAsync(d_sub, tsub.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice, s));
+    RSWR_CUDA(cudaMemcpyAsync(d_lo, tlo.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice, s));
+    RSWR_CUDA(cudaMemcpyAsync(d_hi, thi.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice, s));
+
+    // level 0 (paper Sec. 2.1, or the given state), boundary nodes from the samples
+    if (q0) RSWR_CUDA(cudaMemcpyAsync(X0, q0, es * nx, cudaMemcpyDeviceToDevice, s));
+    else RSWR_CUDA(cudaMemsetAsync(X0, 0, es * nx, s));
+    if (q1) RSWR_CUDA(cudaMemcpyAsync(X1, q1, es * nx, cudaMemcpyDeviceToDevice, s));
+    else if (q0 && e->form == kCanonical) RSWR_CUDA(cudaMemcpyAsync(X1, q0, es * nx, cudaMemcpyDeviceToDevice, s));
+    else RSWR_CUDA(cudaMemsetAsync(X1, 0, es * nx, s));
+    ProblemDev<Real> pb{};
+    pb.base = 0;
+    pb.nx = nx;
+    pb.fA = fA;
+    pb.fB = fB;
+    ProblemDev<Real>* d_pb = reinterpret_cast<ProblemDev<Real>*>(e->d_problems);
+    RSWR_CUDA(cudaMemcpyAsync(d_pb, &pb, sizeof(pb), cudaMemcpyHostToDevice, s));
+    RSWR_CUDA(set_boundary_launch(e->dtype, e->form, X0, X1, d_pb, 1, s));
+    RSWR_CUDA(cudaStreamSynchronize(s));  // pb is on the stack
+
+    PaperParams<Real> pp{};
+    pp.fA = fA;
+    pp.fB = fB;
+    pp.gL = gL;
+    pp.gR = gR;
+    pp.span_min = d_span;
+    pp.tile_sub = d_sub;
+    pp.tile_lo = d_lo;
+    pp.tile_hi = d_hi;
+    pp.nx = nx;
+    pp.N = N;
+    pp.el = el;
+    pp.er = er;
+    pp.tau_stride = tau_max;
+    pp.form = e->form;
+    pp.c2 = sizeof(Real) == 8 ? (Real)ph.c2 : (Real)ph.c2f;
+    pp.k = sizeof(Real) == 8 ? (Real)ph.k : (Real)ph.kf;
+    const double dx = (ph.xb - ph.xa) / (double)(nx - 1);
+    pp.two_dx = (Real)(2.0 * dx);
+    int64_t m_count = 0;
+    for (int64_t n0 = 0; n0 < T;) {
+        const int steps = (int)std::min<int64_t>(tau, T - n0);
+        pp.u = X0;
+        pp.w = X1;
+        pp.n0 = n0;
+        pp.steps = steps;
+        RSWR_CUDA(cudaMemcpyAsync(d_span, &steps, sizeof(int), cudaMemcpyHostToDevice, s));
+        const size_t smem_i = es * (8 * (size_t)(ov + steps + 2)) + sizeof(int) * (size_t)(ov + 2);
+        RSWR_CUDA(paper_iface_launch(e->dtype, &pp, (int)(N - 1), smem_i, s));
+        int span = steps;
+        RSWR_CUDA(cudaMemcpyAsync(&span, d_span, sizeof(int), cudaMemcpyDeviceToHost, s));
+        RSWR_CUDA(cudaStreamSynchronize(s));
+        if (span > cap) span = (int)cap;
+        if (span < 1) span = 1;
+        pp.steps = span;
+        pp.uo = Y0;
+        pp.wo = Y1;
+        const size_t smem_r = es * 4 * (size_t)(CH + 2 * span + 2);
+        RSWR_CUDA(paper_resolve_launch(e->dtype, &pp, (int)nt, smem_r, s));
+        if (spans && m_count < spans_cap) spans[m_count] = span;
+        ++m_count;
+        n0 += span;
+        std::swap(X0, Y0);
+        std::swap(X1, Y1);
+        tau = (int64_t)std::ceil((1.0 + beta) * (double)span);
+        if (tau > tau_max) tau = tau_max;
+    }
+    if (nspans) *nspans = m_count;
+    RSWR_CUDA(cudaMemcpyAsync(out0, X0, es * nx, cudaMemcpyDeviceToDevice, s));
+    RSWR_CUDA(cudaMemcpyAsync(out1, X1, es * nx, cudaMemcpyDeviceToDevice, s));
+    RSWR_CUDA(cudaStreamSynchronize(s));
+    return RSWR_OK;
+}
+
+}  // namespace
+
 void rswr::set_error_message(const char* m) { g_msg = m; }
 
 // ===========================================================================
@@ -1580,6 +1708,27 @@ rswr_status rswr_batch_set_graph(rswr_batch_t batch, int32_t enable)
     if (!batch) return fail(RSWR_EINVAL, "NULL batch");
     batch->e->use_graph = enable != 0;
     return RSWR_OK;
+}
+
+rswr_status rswr_run_paper(rswr_plan_t plan, const void* fA, const void* fB, int64_t T, const void* q0,
+                           const void* q1, void* out0, void* out1, int64_t* spans, int64_t spans_cap,
+                           int64_t* nspans, void* stream)
+{
+    if (!plan) return fail(RSWR_EINVAL, "NULL plan");
+    Engine* e = plan->e;
+    if (T < 0) return fail(RSWR_EINVAL, "T < 0");
+    if (!out0 || !out1) return fail(RSWR_EINVAL, "out0 and out1 are required");
+    const ProbHost& ph = e->probs[0];
+    if (ph.ov + 64 > 2048) return fail(RSWR_EINVAL, "paper-literal path supports overlaps up to 1984 points");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (e->dtype == kF64)
+        return run_paper<double>(e, static_cast<const double*>(fA), static_cast<const double*>(fB), T,
+                                 static_cast<const double*>(q0), static_cast<const double*>(q1),
+                                 static_cast<double*>(out0), static_cast<double*>(out1), spans, spans_cap, nspans,
+                                 0.1, s);
+    return run_paper<float>(e, static_cast<const float*>(fA), static_cast<const float*>(fB), T,
+                            static_cast<const float*>(q0), static_cast<const float*>(q1), static_cast<float*>(out0),
+                            static_cast<float*>(out1), spans, spans_cap, nspans, 0.1, s);
 }
 
 int32_t rswr_variant_count(void) { return span_variant_count(); }

@@ -118,6 +118,27 @@ struct AdjParams {
     long long wait_ns;
 };
 
+// The paper-literal span (paper_kernel.cu): plain (unpadded) state arrays.
+template <typename Real>
+struct PaperParams {
+    const Real* u;   // state pair at level n0
+    const Real* w;
+    Real* uo;        // combined state pair at level n0 + span
+    Real* wo;
+    const Real* fA;
+    const Real* fB;
+    Real* gL;        // [N][tau_stride]: predicted flux for the left input boundary of subdomain i
+    Real* gR;        // [N][tau_stride]: ... for its right input boundary
+    int* span_min;   // global span (atomicMin over interfaces)
+    const int64_t* tile_sub;  // re-solve tiles: subdomain and owned range [lo, hi)
+    const int64_t* tile_lo;
+    const int64_t* tile_hi;
+    int64_t nx, N, el, er, n0, tau_stride;
+    int32_t steps;   // predictive steps (iface kernel) or selected span (re-solve kernel)
+    int32_t form;
+    Real c2, k, two_dx;
+};
+
 struct VariantInfo {
     int dtype;
     int form;
@@ -148,6 +169,10 @@ cudaError_t adj_init_launch(int dtype, int form, void* l0, void* l1, const void*
 // dL/da[p] = 2 c2_p / a_p * sum of the partials of problem p's tiles over all spans
 cudaError_t adj_reduce_launch(const double* partial, int64_t nspans, int64_t ntiles, const int64_t* tile0,
                               const int64_t* tcount, const double* scale, double* out, int nprob, cudaStream_t s);
+
+// paper_kernel.cu
+cudaError_t paper_iface_launch(int dtype, const void* params, int n_iface, size_t smem, cudaStream_t s);
+cudaError_t paper_resolve_launch(int dtype, const void* params, int ntiles, size_t smem, cudaStream_t s);
 
 // rswr_api.cu: sets the message returned by rswr_last_error_message()
 void set_error_message(const char* m);

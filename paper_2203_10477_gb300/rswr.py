@@ -84,6 +84,7 @@ SIGNATURES = {
     "rswr_run": (_st, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "rswr_run_host": (_st, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "rswr_mono": (_st, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
+    "rswr_run_paper": (_st, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "rswr_adjoint": (_st, [_vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp]),
     "rswr_batch_create": (_st, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(Problem), _i32, _i32, ctypes.c_uint32]),
     "rswr_batch_destroy": (None, [_vp]),
@@ -265,6 +266,25 @@ class Plan:
     def run(self, fA, fB, T, **kw):
         """RSWR run (the hot path).  Returns dict(u, w, traces, recv) of device tensors."""
         return self._run(lib().rswr_run, fA, fB, T, **kw)
+
+    def run_paper(self, fA, fB, T, q0=None, q1=None, out=None, stream=None):
+        """The paper-literal RSWR (data-chosen spans).  Returns dict(u, w, spans)."""
+        torch = _torch()
+        dev = self.device
+        fA_ = _as_dev(fA, self.dtype, dev)
+        fB_ = _as_dev(fB, self.dtype, dev)
+        q0_ = _as_dev(q0, self.dtype, dev)
+        q1_ = _as_dev(q1, self.dtype, dev)
+        td = _tdtype(self.dtype)
+        if out is None:
+            out = (torch.empty(self.nx, dtype=td, device=dev), torch.empty(self.nx, dtype=td, device=dev))
+        spans = np.zeros(max(T, 1), np.int64)
+        ns = ctypes.c_int64()
+        with torch.cuda.device(dev):
+            check(lib().rswr_run_paper(self.h, _ptr(fA_), _ptr(fB_), T, _ptr(q0_), _ptr(q1_), _ptr(out[0]),
+                                       _ptr(out[1]), spans.ctypes.data, len(spans), ctypes.addressof(ns),
+                                       _stream(stream)))
+        return {"u": out[0], "w": out[1], "spans": spans[: ns.value].copy()}
 
     def mono(self, fA, fB, T, **kw):
         """Monolithic comparator with the same arguments and results as run()."""

@@ -563,3 +563,41 @@ def test_c5_full_size(R, oracle_mod):
             err = np.linalg.norm(gf[i].astype(np.float64) - ref["dg"]) / np.linalg.norm(ref["dg"])
             print(f"c5 problem {i} FP32 grad_fA rel. 2-norm error {err:.2e} (tolerance {tol:g})")
             assert err <= tol, (i, err)
+
+
+# ----------------------------------------------------------------------------
+# the paper-literal RSWR (data-chosen spans, flux-exchange update)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("form", [CAN, INC])
+@pytest.mark.parametrize("nx,N,ov,cfl,T", [
+    (1001, 2, 16, 0.5, 2000),     # config 1
+    (1001, 10, 16, 0.5, 600),
+    (1001, 4, 24, 0.9, 600),
+    (1001, 3, 9, 0.7, 600),
+    (20001, 16, 32, 0.9, 3000),
+])
+def test_paper_literal_equals_oracle_bitwise(R, oracle_mod, form, nx, N, ov, cfl, T):
+    dt = cfl / (nx - 1)
+    fA = inputs.ramped_sine(T, dt, freq=7.0)
+    z = np.zeros(T + 1)
+    plan = R.Plan(0.0, 1.0, 1.0, nx, dt, N, ov, dtype=F64, form=form)
+    got = plan.run_paper(fA, None, T)
+    ref = oracle_mod.rswr_paper(nx, T, 1.0, dt, fA, z, N, ov, form=ORACLE_FORM[form])
+    assert np.array_equal(got["spans"], ref["spans"]), (got["spans"][:10], ref["spans"][:10])
+    assert_bitwise(host(got["u"]), ref["u"], "paper-literal u")
+    assert_bitwise(host(got["w"]), ref["w"], "paper-literal w")
+    mono = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, z, form=ORACLE_FORM[form])
+    assert np.abs(host(got["u"]) - mono["u"]).max() <= 1e-12 * np.abs(mono["u"]).max()
+
+
+def test_paper_literal_fp32_close_to_fp64(R, oracle_mod):
+    nx, N, ov, T = 20001, 16, 32, 3000
+    dt = 0.9 / (nx - 1)
+    fA = inputs.gaussian_pulse(T, dt, sigma_steps=20)
+    plan = R.Plan(0.0, 1.0, 1.0, nx, dt, N, ov, dtype=F32)
+    got = plan.run_paper(fA, None, T)
+    mono = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, np.zeros(T + 1))
+    err = np.abs(host(got["u"]).astype(np.float64) - mono["u"]).max() / np.abs(mono["u"]).max()
+    assert err <= 1e-5, err
+    assert got["spans"].sum() == T
