@@ -178,6 +178,26 @@ def test_tangent_linear_matches_oracle_adjoint_dc2(oracle_mod):
 # structural properties
 # ----------------------------------------------------------------------------
 
+@pytest.mark.parametrize("form", [CAN, INC])
+def test_sine_mode_started_at_rest(oracle_mod, form):
+    """sin(k pi x) is an eigenvector of the discrete Dirichlet Laplacian with
+    eigenvalue -4 sin^2(k pi dx / 2)/dx^2, so from rest (u^{-1} = u^0) the
+    leapfrog gives u^n = u^0 cos((n + 1/2) th) / cos(th/2) exactly, where
+    cos th = 1 - 2 c^2 sin^2(k pi dx / 2)."""
+    nx, T, c = 201, 333, 0.83
+    dt = c / (nx - 1)
+    x = np.linspace(0.0, 1.0, nx)
+    for kk in (1, 5, 40):
+        u0 = np.sin(kk * np.pi * x)
+        u0[0] = u0[-1] = 0.0
+        z = np.zeros(T + 1)
+        out = oracle_mod.leapfrog(nx, T, 1.0, dt, z, z, q0=u0, form=form, rec_j=[37])
+        th = 2.0 * np.arcsin(c * np.sin(kk * np.pi / (nx - 1) / 2))  # cos th = 1 - 2 c^2 sin^2(.)
+        n = np.arange(T + 1)
+        np.testing.assert_allclose(out["u"], u0 * np.cos((T + 0.5) * th) / np.cos(th / 2), rtol=0, atol=1e-12)
+        np.testing.assert_allclose(out["rec"][0], u0[37] * np.cos((n + 0.5) * th) / np.cos(th / 2), rtol=0, atol=1e-12)
+
+
 def test_discrete_energy_is_conserved(oracle_mod):
     """With u = 0 on both ends the leapfrog conserves
     E^{n+1/2} = ||u^{n+1} - u^n||^2 + c^2 <D u^{n+1}, D u^n>  (D = forward difference)."""
