@@ -118,27 +118,51 @@ __global__ void __launch_bounds__(NT) adjoint_kernel(const __grid_constant__ Adj
                 exchange<Real, P, NW>(u, lft, rgt, xch, buf, warp, lane);
                 buf ^= 1;
                 Real* lp = laps + s * W + tid * P;
+                const bool step = s + 1 < len;
+                // one pass: the Laplacian of this level (from the step's own neighbour
+                // sum, (uL + uR) - 2u = fma(-2, u, uL + uR) exactly) and the step
+                if constexpr (FORM == kCanonical) {
+                    Real ul = lft;
 #pragma unroll
-                for (int i = 0; i < P; ++i) {
-                    const Real ul = i > 0 ? u[i - 1] : lft;
-                    const Real ur = i < P - 1 ? u[i + 1] : rgt;
-                    lp[i] = rsub(radd(ul, ur), rmul(Real(2), u[i]));
-                }
-                if (s + 1 < len) {
-                    const int64_t n = prm.n0 + s;
-                    leap_step<Real, FORM, P>(u, w, lft, rgt, c2, kk);
-                    if (special) {
-                        const Real fa_old = pu.fA ? pu.fA[n] : Real(0), fa_new = pu.fA ? pu.fA[n + 1] : Real(0);
-                        const Real fb_old = pu.fB ? pu.fB[n] : Real(0), fb_new = pu.fB ? pu.fB[n + 1] : Real(0);
-                        patch_special<Real, FORM, P>(u, w, sp, Real(0), Real(0), fa_old, fa_new, fb_old, fb_new);
+                    for (int i = 0; i < P; ++i) {
+                        const Real uc = u[i];
+                        const Real ur = i < P - 1 ? u[i + 1] : rgt;
+                        const Real sum = radd(ul, ur);
+                        lp[i] = rfma(Real(-2), uc, sum);
+                        if (step) {
+                            u[i] = rfma(c2, sum, rfma(kk, uc, -w[i]));
+                            w[i] = uc;
+                        }
+                        ul = uc;
                     }
+                } else {
+                    Real d_prev = rsub(u[0], lft);
+#pragma unroll
+                    for (int i = 0; i < P; ++i) {
+                        const Real ur = i < P - 1 ? u[i + 1] : rgt;
+                        const Real d = rsub(ur, u[i]);
+                        const Real lap = rsub(d, d_prev);
+                        d_prev = d;
+                        lp[i] = lap;
+                        if (step) {
+                            const Real v = rfma(c2, lap, w[i]);
+                            w[i] = v;
+                            u[i] = radd(u[i], v);
+                        }
+                    }
+                }
+                if (step && special) {
+                    const int64_t n = prm.n0 + s;
+                    const Real fa_old = pu.fA ? pu.fA[n] : Real(0), fa_new = pu.fA ? pu.fA[n + 1] : Real(0);
+                    const Real fb_old = pu.fB ? pu.fB[n] : Real(0), fb_new = pu.fB ? pu.fB[n + 1] : Real(0);
+                    patch_special<Real, FORM, P>(u, w, sp, Real(0), Real(0), fa_old, fa_new, fb_old, fb_new);
                 }
             }
         }
         __syncthreads();
 
         // ---- lambda phase: levels m0 .. m0+len-1 pair with u levels n0+len-1 .. n0
-        double acc = 0.0;
+        Real racc = Real(0);
         {
             Real l[P], lw[P];
             smem_to_regs<Real, P>(stage + 2 * W + tid * P, l);
@@ -161,7 +185,7 @@ __global__ void __launch_bounds__(NT) adjoint_kernel(const __grid_constant__ Adj
 #pragma unroll
                 for (int i = 0; i < P; ++i) {
                     const int64_t j = gj + i;
-                    if (j >= jlo && j < jhi) acc += (double)rmul(l[i], lp[i]);
+                    if (j >= jlo && j < jhi) racc = rfma(l[i], lp[i], racc);
                 }
                 if (special) {
                     const Real sval = sp.rs >= 0 ? pl.src[(m + 1) * pl.src_stride] : Real(0);
@@ -178,6 +202,7 @@ __global__ void __launch_bounds__(NT) adjoint_kernel(const __grid_constant__ Adj
             regs_to_smem<Real, P>(stage + 3 * W + tid * P, lw);
         }
         fence_proxy_async_smem();
+        double acc = (double)racc;
         // block reduction of acc in a fixed order
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);

@@ -872,13 +872,24 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     }
     const int64_t slen = at;
     const int64_t nspans = (T + SA - 1) / SA;
-    const int64_t C = std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)std::max<int64_t>(nspans, 1))));
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t arr = up(es * slen);
+    // Checkpoint spacing: every span boundary when all of them fit in half of the
+    // free device memory (no recompute sweep), else sqrt(#spans) of them.
+    int64_t C = std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)std::max<int64_t>(nspans, 1))));
+    {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+            const size_t avail = free_b + e->adj_mem_cap;
+            if ((size_t)(nspans + 6) * 2 * arr < avail / 2) C = 1;
+        } else {
+            cudaGetLastError();
+        }
+    }
     const int64_t nck = std::max<int64_t>(1, (nspans + C - 1) / C);
     const int64_t nstates = nck + C + 4;  // checkpoints | segment | forward work pair | adjoint pair
 
     // one device block: states, partial sums, tables
-    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
-    const size_t arr = up(es * slen);
     const size_t b_states = 2 * arr * nstates;
     const size_t b_partial = up(sizeof(double) * std::max<int64_t>(nspans, 1) * nta);
     const size_t b_tiles = up(sizeof(TileDev) * (ntf + nta));
