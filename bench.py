@@ -56,6 +56,35 @@ def load_peaks() -> dict:
         return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_span_kernel_c2.md")
+KERNEL_SOURCES = ["span_kernel.cu", "span_common.cuh", "rswr_device.cuh", "rswr_internal.h"]
+
+
+def kernel_sha() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2203_10477_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(dtype: str, variant: int, span: int):
+    """DRAM bytes per update of the span kernel from the committed ncu capture,
+    when it was taken on these very kernel sources, variant and span."""
+    try:
+        sha = kernel_sha()
+        for line in open(TRAFFIC_FILE):
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(cells) >= 7 and cells[0] == dtype and cells[1].isdigit():
+                if int(cells[1]) == variant and int(cells[2]) == span and cells[3] == sha:
+                    return float(cells[6])
+    except Exception:
+        return None
+    return None
+
+
 def alu_peaks(sm_mhz: float) -> dict:
     """Arithmetic-pipe-bound LUP rates of the span kernel's fast path.
 
@@ -281,19 +310,22 @@ def e2e_run(torch, plan, p, steps):
     return ms, h2d, d2h
 
 
-def profile_case(which: str, variant=None) -> None:
-    """The workload of the bench at nx = 2^22 and 320 steps (10 spans): state
-    arrays of 32 MiB (FP64) / 16 MiB (FP32) each, four of them, so DRAM counters
-    still see traffic beyond L2, and one span-kernel launch of a few ms."""
+def profile_case(which: str, variant=None, span=None, full=False) -> None:
+    """The bench workload (full = True) or its small version for detailed
+    captures: nx = 2^22 and 320 steps (10 spans), four state arrays of 32 MiB
+    (FP64) / 16 MiB (FP32), so DRAM counters still see traffic beyond L2.  Runs
+    the workload twice (the first run warms up)."""
     import torch
 
     from paper_2203_10477_gb300 import build, rswr
 
     build.build()
-    p = inputs.c2(T=320, nx=1 << 22)
+    p = inputs.c2() if full else inputs.c2(T=320, nx=1 << 22)
     plan = rswr.Plan.from_problem(p, dtype=rswr.F64 if which == "f64" else rswr.F32)
     if variant is not None:
         plan.set_variant(variant)
+    if span is not None:
+        plan.set_span(span)
     for _ in range(2):
         plan.run(p.fA, p.fB, p.T, traces=True)
     torch.cuda.synchronize()
@@ -429,10 +461,12 @@ def main():
     ap.add_argument("--profile-case", choices=["f64", "f32"], default=None,
                     help="run the small profiling case (nx=2^22, 320 steps) twice and exit (for ncu)")
     ap.add_argument("--variant", type=int, default=None, help="kernel variant of the profiling case")
+    ap.add_argument("--span", type=int, default=None, help="steps per span of the profiling case")
+    ap.add_argument("--full", action="store_true", help="profiling case at the bench's full size")
     args = ap.parse_args()
 
     if args.profile_case:
-        profile_case(args.profile_case, args.variant)
+        profile_case(args.profile_case, args.variant, args.span, args.full)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -514,7 +548,7 @@ def main():
     # algorithmic bytes per LUP of RSWR with the subdomain geometry:
     # w * (2 (core + ov) + 2 core) / (core * S), core = nx / N
     core_sub = p.nx / p.n_sub
-    bpl = lambda w: w * (2 * (core_sub + p.overlap) + 2 * core_sub) / (core_sub * info64["span_steps"])
+    bpl = lambda w, S: w * (2 * (core_sub + p.overlap) + 2 * core_sub) / (core_sub * S)
 
     line = {
         "metric": METRIC,
@@ -534,9 +568,9 @@ def main():
                    "traces": "all 1023 interfaces x 2 output waveforms per level",
                    "l2": "flushed between steps (256 MiB write); state > L2",
                    "variant_f64": {k: info64[k] for k in ("variant", "points_per_thread", "threads_per_cta",
-                                                            "window", "core", "mode")},
+                                                            "window", "core", "mode", "span_steps")},
                    "variant_f32": {k: info32[k] for k in ("variant", "points_per_thread", "threads_per_cta",
-                                                            "window", "core", "mode")},
+                                                            "window", "core", "mode", "span_steps")},
                    "replicas": "one independent replica per GPU" if n > 1 else None},
         "pct_stencil_roofline": 100.0 * value64 / n / r_hbm["f64"],
         "stencil_roofline": {"f64_glups": r_hbm["f64"], "f32_glups": r_hbm["f32"],
@@ -545,17 +579,22 @@ def main():
         "roofline": {"bound": "alu", "kernel": "span_kernel<double, canonical>",
                      "achieved": k64, "peak": alu_max["f64"], "unit": "GLUP/s",
                      "frac": k64 / alu_max["f64"], "frac_at_run_clock": k64 / alu_run["f64"],
-                     "traffic": None,
-                     "algorithmic_bytes_per_lup": bpl(8),
-                     "achieved_gbs": k64 * bpl(8),
+                     "traffic": (lambda b: None if b is None else b * lups)(
+                         measured_traffic("f64", info64["variant"], info64["span_steps"])),
+                     "traffic_source": "profiles/traffic_span_kernel_c2.md (bytes/update x updates per launch)",
+                     "algorithmic_bytes_per_lup": bpl(8, info64["span_steps"]),
+                     "achieved_gbs": k64 * bpl(8, info64["span_steps"]),
                      "peak_definition": "152 SMs x 2 FP64 instr/clk x 2070 MHz / 3 FP64 instr per LUP"},
         "f32": {"value": value32, "unit": UNIT, "ms_per_step": 1e3 * t32 / args.steps, "form": "increment",
                 "pct_stencil_roofline": 100.0 * value32 / n / r_hbm["f32"],
                 "error_vs_fp64_oracle": "<= 1e-5 relative (tests/test_gpu_parity.py)",
                 "roofline": {"bound": "alu", "kernel": "span_kernel<float, increment>", "achieved": k32,
                              "peak": alu_max["f32"], "unit": "GLUP/s", "frac": k32 / alu_max["f32"],
-                             "frac_at_run_clock": k32 / alu_run["f32"], "traffic": None,
-                             "algorithmic_bytes_per_lup": bpl(4), "achieved_gbs": k32 * bpl(4),
+                             "frac_at_run_clock": k32 / alu_run["f32"],
+                             "traffic": (lambda b: None if b is None else b * lups)(
+                                 measured_traffic("f32", info32["variant"], info32["span_steps"])),
+                             "algorithmic_bytes_per_lup": bpl(4, info32["span_steps"]),
+                             "achieved_gbs": k32 * bpl(4, info32["span_steps"]),
                              "peak_definition": "152 SMs x 128 FP32 lanes x 2070 MHz / 4 FP32 instr per LUP"}},
         "monolithic": mono,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
