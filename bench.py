@@ -312,20 +312,28 @@ def e2e_run(torch, plan, p, steps):
 
 def profile_case(which: str, variant=None, span=None, full=False) -> None:
     """The bench workload (full = True) or its small version for detailed
-    captures: nx = 2^22 and 320 steps (10 spans), four state arrays of 32 MiB
-    (FP64) / 16 MiB (FP32), so DRAM counters still see traffic beyond L2.  Runs
-    the workload twice (the first run warms up)."""
+    captures: nx = 2^22, 256 subdomains (the bench's subdomain length of 16384
+    points, so the same share of tiles carries interface probes) and 320 steps
+    (10 spans); four state arrays of 32 MiB (FP64) / 16 MiB (FP32), so DRAM
+    counters still see traffic beyond L2.  Runs the workload twice (the first
+    run warms up)."""
+    import dataclasses
+
     import torch
 
     from paper_2203_10477_gb300 import build, rswr
 
     build.build()
-    p = inputs.c2() if full else inputs.c2(T=320, nx=1 << 22)
+    if full:
+        p = inputs.c2()
+    else:
+        p = inputs.c2(T=320, nx=1 << 22)
+        p = dataclasses.replace(p, n_sub=p.nx // 16384)
     plan = rswr.Plan.from_problem(p, dtype=rswr.F64 if which == "f64" else rswr.F32)
-    if variant is not None:
-        plan.set_variant(variant)
     if span is not None:
         plan.set_span(span)
+    if variant is not None:
+        plan.set_variant(variant)
     for _ in range(2):
         plan.run(p.fA, p.fB, p.T, traces=True)
     torch.cuda.synchronize()

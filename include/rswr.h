@@ -129,7 +129,10 @@ rswr_status rswr_plan_get_info(rswr_plan_t plan, rswr_plan_info* info);
 rswr_status rswr_plan_set_span(rswr_plan_t plan, int32_t S);
 
 /* Kernel variant (points per thread x threads per CTA) for the plan's dtype
- * and form; see rswr_variant_count / rswr_variant_get.  Re-tiles the grid. */
+ * and form; see rswr_variant_count / rswr_variant_get.  Re-tiles the grid.
+ * RSWR_EINVAL when the variant cannot run the plan's span (its max_span,
+ * rswr_variant_get_tiling).  rswr_plan_set_span moves a plan whose variant
+ * cannot run the new span to the default variant for it. */
 rswr_status rswr_plan_set_variant(rswr_plan_t plan, int32_t variant);
 rswr_status rswr_plan_set_mode(rswr_plan_t plan, int32_t mode);
 
@@ -322,6 +325,15 @@ int32_t rswr_variant_count(void);
  * and threads per CTA of variant v. */
 rswr_status rswr_variant_get(int32_t v, int32_t* dtype, int32_t* form, int32_t* points_per_thread,
                              int32_t* threads_per_cta);
+/* Tiling of variant v: warp halo (0: warps exchange neighbour values every
+ * step; > 0: warp windows overlap by twice this many points), points per CTA
+ * window, longest span the variant runs (0: any span whose halo fits the
+ * window; > 0: at most this many steps, because its warps never exchange data
+ * inside a span) and threads per CTA at launch (threads_per_cta compute
+ * threads, plus 32 for variants with a producer warp that moves the windows).
+ * Any pointer may be NULL.  RSWR_EINVAL for v out of range. */
+rswr_status rswr_variant_get_tiling(int32_t v, int32_t* warp_halo, int32_t* window, int32_t* max_span,
+                                    int32_t* threads_launched);
 
 #ifdef __cplusplus
 }

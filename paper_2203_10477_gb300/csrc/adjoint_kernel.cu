@@ -268,7 +268,7 @@ AEntry make_aentry()
 {
     constexpr int W = NT * P;
     AEntry e;
-    e.info = VariantInfo{sizeof(Real) == 8 ? kF64 : kF32, FORM, P, NT, 0, NT * P};
+    e.info = VariantInfo{sizeof(Real) == 8 ? kF64 : kF32, FORM, P, NT, 0, NT * P, NT, 0};
     e.SA = SA;
     e.fn = reinterpret_cast<const void*>(&adjoint_kernel<Real, FORM, P, NT, SA>);
     e.smem = sizeof(Real) * ((4 + SA) * W + 4 * (NT / 32));

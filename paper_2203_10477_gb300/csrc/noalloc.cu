@@ -111,12 +111,14 @@ rswr_status run_noalloc(const rswr_problem& q, int form, const void* fA, const v
     const float kf = 2.0f - 2.0f * c2f;
     if (!(c <= 1.0)) return nfail(RSWR_ECFL, "Courant number a*dt/dx > 1");
 
-    // kernel variant and tiling: the default variant of this dtype/form, one launch per span
+    // kernel variant and tiling: the default variant of this dtype/form for the
+    // span S = floor(overlap / 2), one launch per span
     const int dtype = sizeof(Real) == 8 ? kF64 : kF32;
+    const int S = q.overlap / 2 < 256 ? q.overlap / 2 : 256;
     int v = -1;
     for (int i = 0; i < span_variant_count(); ++i) {
         const VariantInfo vi = span_variant_info(i);
-        if (vi.dtype == dtype && vi.form == form) {
+        if (vi.dtype == dtype && vi.form == form && (vi.max_span == 0 || S <= vi.max_span)) {
             v = i;
             break;
         }
@@ -124,7 +126,6 @@ rswr_status run_noalloc(const rswr_problem& q, int form, const void* fA, const v
     if (v < 0) return nfail(RSWR_ENOTSUP, "no kernel variant for this dtype/form");
     const VariantInfo vi = span_variant_info(v);
     const int W = vi.W;
-    const int S = q.overlap / 2 < 256 ? q.overlap / 2 : 256;
     const int H = (S + 3) / 4 * 4;
     const int core = W - 2 * H;
     if (core < H || core < 4) return nfail(RSWR_EINVAL, "overlap too large for the CTA window");

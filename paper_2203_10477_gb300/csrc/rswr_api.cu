@@ -149,12 +149,14 @@ void free_engine(Engine* e)
     delete e;
 }
 
-int default_variant(int dtype, int form)
+bool variant_takes_span(const VariantInfo& vi, int S) { return vi.max_span == 0 || S <= vi.max_span; }
+
+int default_variant(int dtype, int form, int S)
 {
-    // first registered variant of the dtype/form is the default
+    // first registered variant of the dtype/form that runs spans of S steps
     for (int v = 0; v < span_variant_count(); ++v) {
         const VariantInfo vi = span_variant_info(v);
-        if (vi.dtype == dtype && vi.form == form) return v;
+        if (vi.dtype == dtype && vi.form == form && variant_takes_span(vi, S)) return v;
     }
     return -1;
 }
@@ -169,6 +171,7 @@ rswr_status layout(Engine* e)
     e->W = vi.W;
     e->H = (e->S + 3) / 4 * 4;
     e->core = e->W - 2 * e->H;
+    if (!variant_takes_span(vi, e->S)) return fail(RSWR_EINVAL, "span longer than the warp halo of this variant");
     if (e->core < e->H || e->core < 4) return fail(RSWR_EINVAL, "span too long for the CTA window of this variant");
     const int64_t pad = e->H + 8;
     int64_t at = 0, tile = 0, off = 0;
@@ -267,7 +270,7 @@ rswr_status make_engine(Engine** out, int nprob, const rswr_problem* pr, int32_t
         S = std::min(S, pr[p].overlap / 2);
     }
     e->S = std::min(S, kSpanCap);
-    e->variant = default_variant(e->dtype, e->form);
+    e->variant = default_variant(e->dtype, e->form, e->S);
     if (e->variant < 0) {
         delete e;
         return fail(RSWR_ENOTSUP, "no kernel variant for this dtype/form");
@@ -1451,11 +1454,14 @@ rswr_status rswr_plan_set_span(rswr_plan_t plan, int32_t S)
     Engine* e = plan->e;
     if (S < 1 || S > e->probs[0].ov / 2 || S > kSpanCap)
         return fail(RSWR_EOVERLAP, "span must satisfy 1 <= S <= floor(overlap/2)");
-    const int old = e->S;
+    const int old = e->S, oldv = e->variant;
     e->S = S;
-    rswr_status st = layout(e);
+    // a variant whose warp halo is shorter than S gives way to the default one for S
+    if (!variant_takes_span(span_variant_info(e->variant), S)) e->variant = default_variant(e->dtype, e->form, S);
+    rswr_status st = e->variant >= 0 ? layout(e) : fail(RSWR_ENOTSUP, "no kernel variant runs this span");
     if (st != RSWR_OK) {
         e->S = old;
+        e->variant = oldv;
         layout(e);
     }
     return st;
@@ -1753,6 +1759,18 @@ rswr_status rswr_variant_get(int32_t v, int32_t* dtype, int32_t* form, int32_t* 
     if (form) *form = vi.form == kCanonical ? RSWR_FORM_CANONICAL : RSWR_FORM_INCREMENT;
     if (points_per_thread) *points_per_thread = vi.P;
     if (threads_per_cta) *threads_per_cta = vi.NT;
+    return RSWR_OK;
+}
+
+rswr_status rswr_variant_get_tiling(int32_t v, int32_t* warp_halo, int32_t* window, int32_t* max_span,
+                                    int32_t* threads_launched)
+{
+    if (v < 0 || v >= span_variant_count()) return fail(RSWR_EINVAL, "variant out of range");
+    const VariantInfo vi = span_variant_info(v);
+    if (warp_halo) *warp_halo = vi.KH;
+    if (window) *window = vi.W;
+    if (max_span) *max_span = vi.max_span;
+    if (threads_launched) *threads_launched = vi.threads;
     return RSWR_OK;
 }
 

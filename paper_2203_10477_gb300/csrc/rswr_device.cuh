@@ -60,6 +60,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
+// Plain arrival (no transaction bytes).
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 // Waits for the phase with the given parity to complete; gives up after
 // limit_ns nanoseconds (returns false) or as soon as another CTA latched an
 // error (err_code != 0).
@@ -75,6 +81,25 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
             // keep waiting a little: the copy was issued and normally lands
             if (global_ns() - t0 > (limit_ns >> 4)) return false;
         }
+    }
+}
+
+// The same wait for a thread that has nothing else to do (a producer): it
+// sleeps between polls (64 ns growing to 512 ns) so that it takes almost no
+// issue slots from the warps that compute.
+__device__ __forceinline__ bool mbar_wait_backoff(uint64_t* bar, uint32_t parity, long long limit_ns,
+                                                  const volatile int* err_code)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = global_ns();
+    unsigned ns = 64;
+    for (;;) {
+        __nanosleep(ns);
+        if (ns < 512) ns <<= 1;
+        if (mbar_try_wait(bar, parity)) return true;
+        const long long dt = global_ns() - t0;
+        if (dt > limit_ns) return false;
+        if (err_code && *err_code != 0 && dt > (limit_ns >> 4)) return false;
     }
 }
 
@@ -112,6 +137,41 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 
 // Same for global memory (flag hand-off between bulk copies of different CTAs).
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// ---- named barriers ---------------------------------------------------------
+// Barrier 1 among the first NB threads of the CTA (NB a multiple of 32); the
+// other threads of the CTA never touch it.  NB = 0 means the whole CTA
+// (__syncthreads, barrier 0).
+template <int NB>
+__device__ __forceinline__ void block_sync()
+{
+    if constexpr (NB == 0) {
+        __syncthreads();
+    } else {
+        static_assert(NB % 32 == 0, "named barriers count whole warps");
+        asm volatile("barrier.cta.sync 1, %0;" ::"n"(NB) : "memory");
+    }
+}
+
+// block_sync that also returns whether any participating thread passed p = true.
+template <int NB>
+__device__ __forceinline__ bool block_sync_or(bool p)
+{
+    if constexpr (NB == 0) {
+        return __syncthreads_or(p) != 0;
+    } else {
+        uint32_t r;
+        asm volatile(
+            "{\n\t.reg .pred a, b;\n\t"
+            "setp.ne.u32 a, %1, 0;\n\t"
+            "barrier.cta.red.or.pred b, 1, %2, a;\n\t"
+            "selp.u32 %0, 1, 0, b;\n\t}"
+            : "=r"(r)
+            : "r"((uint32_t)p), "n"(NB)
+            : "memory");
+        return r != 0;
+    }
+}
 
 // ---- acquire / release flags ---------------------------------------------
 __device__ __forceinline__ int ld_acquire(const int* p)

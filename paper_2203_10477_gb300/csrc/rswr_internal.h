@@ -146,6 +146,8 @@ struct VariantInfo {
     int NT;  // threads per CTA
     int KH;  // warp halo (0: warps exchange neighbours every step)
     int W;   // points per CTA window
+    int threads;   // threads per CTA at launch (NT, or NT + a producer warp)
+    int max_span;  // longest span the variant runs (0: any that fits the window)
 };
 
 // span_kernel.cu

@@ -71,7 +71,8 @@ __device__ __forceinline__ void regs_to_smem(Real* s, const Real (&r)[P])
 // Neighbour values of the thread's first and last point: warp shuffles inside
 // a warp, one shared slot per warp edge across warps.  At the two window ends
 // the ghost mirrors the interior neighbour (zero-flux prediction guess).
-template <typename Real, int P, int NW>
+// BAR: the barrier the window's warps share (block_sync).
+template <typename Real, int P, int NW, int BAR = 0>
 __device__ __forceinline__ void exchange(const Real (&u)[P], Real& lft, Real& rgt, Real* xch, int buf, int warp,
                                          int lane)
 {
@@ -80,7 +81,7 @@ __device__ __forceinline__ void exchange(const Real (&u)[P], Real& lft, Real& rg
     Real* slot = xch + buf * NW * 2;
     if (lane == 0) slot[warp * 2 + 0] = u[0];
     if (lane == 31) slot[warp * 2 + 1] = u[P - 1];
-    __syncthreads();
+    block_sync<BAR>();
     if (lane == 0) lft = (warp > 0) ? slot[(warp - 1) * 2 + 1] : u[1];
     if (lane == 31) rgt = (warp < NW - 1) ? slot[(warp + 1) * 2 + 0] : u[P - 2];
 }
@@ -171,7 +172,7 @@ __device__ __forceinline__ void patch_special(Real (&u)[P], Real (&w)[P], const 
 // its interior points 1..P-2, waits at the block barrier, then fetches the
 // cross-warp halos and updates points 0 and P-1.  Every update is the same
 // expression on the same operands as leap_step(), so the bits are identical.
-template <typename Real, int FORM, int P, int NW>
+template <typename Real, int FORM, int P, int NW, int BAR = 0>
 __device__ __forceinline__ void split_step(Real (&u)[P], Real (&w)[P], Real c2, Real k, Real* xch, int buf,
                                            int warp, int lane)
 {
@@ -194,7 +195,7 @@ __device__ __forceinline__ void split_step(Real (&u)[P], Real (&w)[P], Real c2, 
             w[i] = v;
             u[i] = radd(u[i], v);
         }
-        __syncthreads();
+        block_sync<BAR>();
         if (lane == 0) lft = (warp > 0) ? slot[(warp - 1) * 2 + 1] : m_l;
         if (lane == 31) rgt = (warp < NW - 1) ? slot[(warp + 1) * 2 + 0] : m_r;
         {
@@ -218,7 +219,7 @@ __device__ __forceinline__ void split_step(Real (&u)[P], Real (&w)[P], Real c2, 
             u[i] = un;
             ul = uc;
         }
-        __syncthreads();
+        block_sync<BAR>();
         if (lane == 0) lft = (warp > 0) ? slot[(warp - 1) * 2 + 1] : m_l;
         if (lane == 31) rgt = (warp < NW - 1) ? slot[(warp + 1) * 2 + 0] : m_r;
         u[0] = rfma(c2, radd(lft, m_l), rfma(k, u0, -w[0]));
@@ -274,23 +275,74 @@ __device__ __forceinline__ void owned_probes(const ProbeDev<Real>* sp, int np, i
     }
 }
 
+// u[r-1], u[r], u[r+1] of a register index r known only at run time: a
+// binary tree of branches on r (log2 P compares, then three moves) instead of
+// P-way selects; only the owner thread of a probe takes it.
+template <typename Real, int P, int LO, int HI>
+__device__ __forceinline__ void pick3(const Real (&u)[P], Real lft, Real rgt, int r, Real& um, Real& uc, Real& up)
+{
+    if constexpr (HI - LO == 1) {
+        uc = u[LO];
+        um = LO > 0 ? u[LO > 0 ? LO - 1 : 0] : lft;
+        up = LO < P - 1 ? u[LO < P - 1 ? LO + 1 : P - 1] : rgt;
+    } else {
+        constexpr int MID = (LO + HI) / 2;
+        if (r < MID) pick3<Real, P, LO, MID>(u, lft, rgt, r, um, uc, up);
+        else pick3<Real, P, MID, HI>(u, lft, rgt, r, um, uc, up);
+    }
+}
+
 template <typename Real, int P>
 __device__ __forceinline__ void record_owned(const Real (&u)[P], Real lft, Real rgt, const ProbeDev<Real>& pr,
                                              int64_t wabs, int tb, int64_t n)
 {
     const int r = (int)(pr.gidx - wabs - (int64_t)tb);
-    Real um = lft, uc = u[0], up = rgt;
-#pragma unroll
-    for (int i = 0; i < P; ++i) {
-        if (i == r) {
-            uc = u[i];
-            um = (i > 0) ? u[i - 1] : lft;
-            up = (i < P - 1) ? u[i + 1] : rgt;
-        }
-    }
+    Real um, uc, up;
+    pick3<Real, P, 0, P>(u, lft, rgt, r, um, uc, up);
     Real val = (pr.kind == 0) ? uc : rsub(up, um);
     val = rmul(val, pr.scale);
     if (n <= pr.nmax) pr.out[n * pr.stride] = val;
+}
+
+// A probe owned by this thread, prepared once per tile: `ptr` is the output
+// of the current level and advances by `stride` every step; `count` levels of
+// the span are recorded (the probe stops at its nmax).
+template <typename Real>
+struct OwnedProbe {
+    Real* ptr;
+    int64_t stride;
+    Real scale;
+    int r;       // register index of the probed point
+    int kind;    // 0: u_j, 1: u_{j+1} - u_{j-1}
+    int count;
+};
+
+template <typename Real>
+__device__ __forceinline__ OwnedProbe<Real> own_probe(const ProbeDev<Real>& pr, int64_t wabs, int tb, int64_t n0,
+                                                      int steps)
+{
+    OwnedProbe<Real> o;
+    o.r = (int)(pr.gidx - wabs - (int64_t)tb);
+    o.kind = pr.kind;
+    o.scale = pr.scale;
+    o.stride = pr.stride;
+    const int64_t c = pr.nmax - n0 + 1;
+    o.count = c < 0 ? 0 : (c > steps ? steps : (int)c);
+    o.ptr = o.count > 0 ? pr.out + n0 * pr.stride : pr.out;
+    return o;
+}
+
+// Records level n0 + s (called once per step, s = 0, 1, ...).
+template <typename Real, int P>
+__device__ __forceinline__ void record_step(OwnedProbe<Real>& o, const Real (&u)[P], Real lft, Real rgt, int s)
+{
+    if (s < o.count) {
+        Real um, uc, up;
+        pick3<Real, P, 0, P>(u, lft, rgt, o.r, um, uc, up);
+        const Real val = (o.kind == 0) ? uc : rsub(up, um);
+        *o.ptr = rmul(val, o.scale);
+        o.ptr += o.stride;
+    }
 }
 
 // Overlapping warp windows (KH > 0): warp w covers window points
@@ -299,7 +351,7 @@ __device__ __forceinline__ void record_owned(const Real (&u)[P], Real lft, Real 
 // points through shared memory (double-buffered slots, one block barrier);
 // in between, warps advance with shuffles only and the contamination from
 // their window ends stays inside the halos.
-template <typename Real, int P, int NW, int KH>
+template <typename Real, int P, int NW, int KH, int BAR = 0>
 __device__ __forceinline__ void refresh_halos(Real (&u)[P], Real (&w)[P], Real* hx, int buf, int warp, int lane)
 {
     static_assert(P >= 2 * KH, "a thread must hold a halo and the owned points next to it");
@@ -332,7 +384,7 @@ __device__ __forceinline__ void refresh_halos(Real (&u)[P], Real (&w)[P], Real* 
             sw[k] = vw;
         }
     }
-    __syncthreads();
+    block_sync<BAR>();
     if ((lane == 0 && warp > 0) || (lane == 31 && warp < NW - 1)) {
         const int src = lane == 0 ? ((warp - 1) * 2 + 1) : ((warp + 1) * 2 + 0);
         const V* su = reinterpret_cast<const V*>(b + (src * 2 + 0) * KH);

@@ -29,6 +29,7 @@
 // edge per step || TMA store of the core (stage x).
 
 #include <cstdio>
+#include <type_traits>
 
 #include "rswr_internal.h"
 #include "span_common.cuh"
@@ -121,13 +122,183 @@ __device__ __forceinline__ void publish(const SpanParams<Real>& prm, long long t
 
 // Window geometry of a variant: KH = 0 -> warps tile the window back to back;
 // KH > 0 -> warp windows overlap by 2 KH points (see refresh_halos).
+// FREE: the warp halo is at least the span (P < 2 KH: a thread cannot hold a
+// halo and the owned points next to it, so halos are never refreshed and the
+// span is limited to KH steps).
 template <int P, int NT, int KH>
 struct Geom {
     static constexpr int NW = NT / 32;
+    static constexpr bool FREE = KH > 0 && P < 2 * KH;
     static constexpr int CW = KH == 0 ? 32 * P : 32 * P - 2 * KH;  // window offset between warps
     static constexpr int W = KH == 0 ? NT * P : NW * CW + 2 * KH;   // points per CTA window
-    static constexpr int XCH = ((4 * NW + 15) / 16) * 16 + 8 * NW * KH;  // exchange slots (values)
+    static constexpr int XCH = ((4 * NW + 15) / 16) * 16 + (FREE ? 0 : 8 * NW * KH);  // exchange slots (values)
 };
+
+// The predict phase of one tile (Sec. 2.3): `steps` leapfrog steps of the
+// thread's P points u, w (window index tb of its first point), with the
+// tile's probes recorded at every level and the special points (Dirichlet
+// nodes, source, points outside the grid) patched after every step.
+// BAR is the barrier the window's warps share (block_sync); every branch
+// below that contains one depends on per-tile values only, so all threads of
+// the window take it together.  The step loop is instantiated four times
+// (probes yes/no x special points yes/no) so that a plain interior tile runs
+// the bare stencil with no per-step tests.
+template <typename Real, int FORM, int P, int NW, int KH, int PK, int BAR>
+__device__ __forceinline__ void predict_tile(const SpanParams<Real>& prm, const ProblemDev<Real>& pr,
+                                             const TileDev& td, Real (&u)[P], Real (&w)[P], int64_t gj0, int64_t n0,
+                                             int steps, int tb, int own_lo, int own_hi,
+                                             const ProbeDev<Real>* tprobes, int np, Real* xch, Real* hx, int warp,
+                                             int lane, bool edge)
+{
+    constexpr int CW = KH == 0 ? 32 * P : 32 * P - 2 * KH;
+    constexpr int W = KH == 0 ? NW * 32 * P : NW * CW + 2 * KH;
+    const int64_t nx = pr.nx;
+    const int64_t wabs = pr.base + gj0;
+    const int64_t gj = gj0 + tb;
+    const bool has_src = pr.js >= 0 && pr.js >= gj0 && pr.js < gj0 + W;
+    const bool slow = edge || has_src;
+    const bool has_probe = np > 0;
+    const bool few_probes = np <= kTileProbes;
+    const Real c2 = pr.c2, kk = pr.k;
+
+    const bool many_probes = has_probe && !few_probes;
+
+    // special points of this thread (edge / source tiles only)
+    auto special_points = [&]() {
+        Special sp{-1, -1, -1, 0, P - 1};
+        const int64_t lo = gj;
+        auto loc = [&](int64_t j) -> int { return (j >= lo && j < lo + P) ? (int)(j - lo) : -1; };
+        sp.r0 = loc(0);
+        sp.r1 = loc(nx - 1);
+        sp.rs = has_src ? loc(pr.js) : -1;
+        sp.rlo = (int)(lo >= 0 ? 0 : (-lo > P ? P : -lo));
+        sp.rhi = (int)(nx - 1 - lo >= P - 1 ? P - 1 : (nx - 1 - lo < -1 ? -1 : nx - 1 - lo));
+        return sp;
+    };
+
+    int buf = 0;
+    // steps [s_begin, s_end) of the span; PR: record probes, SP: patch special
+    // points.  What only PR or SP needs is set up inside its instantiation.
+    auto run = [&](auto probe_c, auto special_c, int s_begin, int s_end) {
+        constexpr bool PR = decltype(probe_c)::value;
+        constexpr bool SP = decltype(special_c)::value;
+        // probes this thread owns: two in registers, any further ones read from shared memory
+        OwnedProbe<Real> op0{}, op1{};
+        int nown = 0;
+        uint32_t more = 0u;
+        if constexpr (PR) {
+            if (few_probes) {
+                for (int q = 0; q < np; ++q) {
+                    const int64_t li = tprobes[q].gidx - wabs - (int64_t)tb;
+                    if (li >= own_lo && li < own_hi) {
+                        if (nown == 0) op0 = own_probe<Real>(tprobes[q], wabs, tb, n0 + s_begin, s_end - s_begin);
+                        else if (nown == 1) op1 = own_probe<Real>(tprobes[q], wabs, tb, n0 + s_begin, s_end - s_begin);
+                        else more |= 1u << q;
+                        ++nown;
+                    }
+                }
+            }
+        }
+        Special sp{-1, -1, -1, 0, P - 1};
+        if constexpr (SP) sp = special_points();
+        for (int s = s_begin; s < s_end; ++s) {
+            Real lft, rgt;
+            if constexpr (KH > 0) {
+                warp_neighbours<Real, P>(u, lft, rgt, lane);
+            } else {
+                exchange<Real, P, NW, BAR>(u, lft, rgt, xch, buf, warp, lane);
+                buf ^= 1;
+            }
+            const int64_t n = n0 + s;
+            if constexpr (PR) {
+                if (nown > 0) record_step<Real, P>(op0, u, lft, rgt, s - s_begin);
+                if (nown > 1) record_step<Real, P>(op1, u, lft, rgt, s - s_begin);
+                for (uint32_t m = more; m != 0u; m &= m - 1u)
+                    record_owned<Real, P>(u, lft, rgt, tprobes[__ffs(m) - 1], wabs, tb, n);
+                if (many_probes)
+                    record_probes<Real, P>(u, lft, rgt, wabs, tb, own_lo, own_hi, td.probe_begin, td.probe_end,
+                                           prm.probes, n);
+            }
+            if constexpr (SP) {
+                Real uold_s = Real(0), sval = Real(0);
+                if (sp.rs >= 0) {
+                    sval = pr.src[(n + 1) * pr.src_stride];
+                    if constexpr (FORM == kIncrement) uold_s = select_reg<Real, P>(u, sp.rs);
+                }
+                const Real fa_old = pr.fA ? pr.fA[n] : Real(0);
+                const Real fa_new = pr.fA ? pr.fA[n + 1] : Real(0);
+                const Real fb_old = pr.fB ? pr.fB[n] : Real(0);
+                const Real fb_new = pr.fB ? pr.fB[n + 1] : Real(0);
+                leap_step<Real, FORM, P>(u, w, lft, rgt, c2, kk);
+                patch_special<Real, FORM, P>(u, w, sp, uold_s, sval, fa_old, fa_new, fb_old, fb_new);
+            } else {
+                leap_step<Real, FORM, P>(u, w, lft, rgt, c2, kk);
+            }
+        }
+    };
+    // The instantiation is chosen from per-tile values only: every lane of a
+    // warp (and, with exchange(), every thread of the window) must execute the
+    // same shuffle and barrier instructions.  On a slow tile every thread runs
+    // the patching loop; for a thread without special points the patch is a no-op.
+    using Yes = std::true_type;
+    using No = std::false_type;
+    auto run_steps = [&](int s_begin, int s_end) {
+        if (has_probe) {
+            if (slow) run(Yes{}, Yes{}, s_begin, s_end);
+            else run(Yes{}, No{}, s_begin, s_end);
+        } else {
+            if (slow) run(No{}, Yes{}, s_begin, s_end);
+            else run(No{}, No{}, s_begin, s_end);
+        }
+    };
+
+    if constexpr (KH > 0) {
+        if constexpr (PK && FORM == kIncrement && sizeof(Real) == 4 && P >= 2 * KH) {
+            if (!slow && !has_probe) {
+                packed_increment_steps<P, NW, KH>(u, w, c2, steps, hx, buf, warp, lane);
+                return;
+            }
+        }
+        if constexpr (P >= 2 * KH) {
+            // warp halos refreshed every KH steps
+            for (int s0 = 0; s0 < steps; s0 += KH) {
+                if (s0 > 0) {
+                    refresh_halos<Real, P, NW, KH, BAR>(u, w, hx, buf, warp, lane);
+                    buf ^= 1;
+                }
+                run_steps(s0, (s0 + KH < steps) ? s0 + KH : steps);
+            }
+        } else {
+            // free warp windows: the warp halo covers the whole span (steps <= KH,
+            // checked by the caller), so warps never exchange data inside a span
+            run_steps(0, steps);
+        }
+    } else {
+        if (!slow && !has_probe) {
+            // interior tile: halo latency hidden behind the interior updates
+            for (int s = 0; s < steps; ++s) {
+                split_step<Real, FORM, P, NW, BAR>(u, w, c2, kk, xch, buf, warp, lane);
+                buf ^= 1;
+            }
+        } else {
+            run_steps(0, steps);
+        }
+    }
+}
+
+// Registers [own_lo, own_hi) of a thread that it owns: warp w owns its window
+// minus KH halo points at each end that has a neighbouring warp (the outer
+// halos of the first and last warp have no neighbour and belong to them).
+// When KH > P the halo spans several threads, some of which own nothing.
+template <int P, int NW, int KH>
+__device__ __forceinline__ void owned_range(int warp, int lane, int& own_lo, int& own_hi)
+{
+    const int lo_w = (KH > 0 && warp > 0) ? KH : 0;
+    const int hi_w = (KH > 0 && warp < NW - 1) ? 32 * P - KH : 32 * P;
+    const int a = lo_w - lane * P, b = hi_w - lane * P;
+    own_lo = a < 0 ? 0 : (a > P ? P : a);
+    own_hi = b < 0 ? 0 : (b > P ? P : b);
+}
 
 template <typename Real, int FORM, int P, int NT, int KH, int PK, int MINB>
 __global__ void __launch_bounds__(NT, MINB) span_kernel(const __grid_constant__ SpanParams<Real> prm)
@@ -136,6 +307,7 @@ __global__ void __launch_bounds__(NT, MINB) span_kernel(const __grid_constant__ 
     constexpr int W = G::W;
     constexpr int NW = G::NW;
     static_assert(W % 4 == 0, "windows must span whole 16-byte units");
+    static_assert(KH == 0 || P >= 2 * KH, "this kernel refreshes warp halos");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Real* stage = reinterpret_cast<Real*>(smem_raw);  // [2 stages][2 components][W]
     Real* xch = stage + 4 * W;                        // [2 buffers][NW][2]  (+ halo slots when KH > 0)
@@ -215,22 +387,13 @@ __global__ void __launch_bounds__(NT, MINB) span_kernel(const __grid_constant__ 
         const int tile = (int)(t % prm.ntiles);
         const TileDev td = prm.tiles[tile];
         const ProblemDev<Real>& pr = prm.problems[td.problem];
-        const int64_t nx = pr.nx;
         const int64_t gj0 = (int64_t)td.local * prm.core - prm.H;  // problem coordinate of window start
-        const int64_t wabs = pr.base + gj0;
         const int64_t n0 = (int64_t)k * prm.S;
         const int steps = (int)((prm.T - n0 < prm.S) ? (prm.T - n0) : prm.S);
-        const bool edge = (gj0 <= 0) || (gj0 + W - 1 >= nx - 1);
-        const bool has_src = pr.js >= 0 && pr.js >= gj0 && pr.js < gj0 + W;
-        const bool slow = edge || has_src;
-        const bool has_probe = td.probe_end > td.probe_begin;
-        const Real c2 = pr.c2, kk = pr.k;
+        const bool edge = (gj0 <= 0) || (gj0 + W - 1 >= pr.nx - 1);
         const int tb = warp * G::CW + lane * P;  // window index of the thread's first point
-        const int64_t gj = gj0 + tb;
-        // registers this thread owns (the others are a warp halo, KH > 0); the
-        // outer halos of the first and last warp have no neighbour and belong to them
-        const int own_lo = (KH > 0 && lane == 0 && warp > 0) ? KH : 0;
-        const int own_hi = (KH > 0 && lane == 31 && warp < NW - 1) ? P - KH : P;
+        int own_lo, own_hi;
+        owned_range<P, NW, KH>(warp, lane, own_lo, own_hi);
 
         Real* su = stage + x * 2 * W;
         Real* sw = su + W;
@@ -238,114 +401,15 @@ __global__ void __launch_bounds__(NT, MINB) span_kernel(const __grid_constant__ 
         smem_to_regs<Real, P>(su + tb, u);
         smem_to_regs<Real, P>(sw + tb, w);
 
-        // probes of this tile: staged in shared memory, owners found once
+        // probes of this tile: staged in shared memory
         const int np = td.probe_end - td.probe_begin;
-        const bool few_probes = np <= kTileProbes;
-        int pq0 = -1, pq1 = -1;
-        if (has_probe && few_probes) {
+        if (np > 0 && np <= kTileProbes) {
             if (tid < np) s_probes[tid] = prm.probes[td.probe_begin + tid];
             __syncthreads();
-            owned_probes<Real, P>(s_probes, np, wabs, tb, own_lo, own_hi, pq0, pq1);
         }
 
-        // ---- predict: S leapfrog steps of the window
-        // special points of this thread (edge / source tiles only)
-        Special sp{-1, -1, -1, 0, P - 1};
-        bool special = false;
-        if (slow) {
-            const int64_t lo = gj;
-            auto loc = [&](int64_t j) -> int { return (j >= lo && j < lo + P) ? (int)(j - lo) : -1; };
-            sp.r0 = loc(0);
-            sp.r1 = loc(nx - 1);
-            sp.rs = has_src ? loc(pr.js) : -1;
-            sp.rlo = (int)(lo >= 0 ? 0 : (-lo > P ? P : -lo));
-            sp.rhi = (int)(nx - 1 - lo >= P - 1 ? P - 1 : (nx - 1 - lo < -1 ? -1 : nx - 1 - lo));
-            special = sp.r0 >= 0 || sp.r1 >= 0 || sp.rs >= 0 || sp.rlo > 0 || sp.rhi < P - 1;
-        }
-
-        // ---- predict: S leapfrog steps of the window
-        int buf = 0;
-        bool done_packed = false;
-        if constexpr (PK && KH > 0 && FORM == kIncrement && sizeof(Real) == 4) {
-            if (!slow && !has_probe) {
-                packed_increment_steps<P, NW, KH>(u, w, c2, steps, hx, buf, warp, lane);
-                done_packed = true;
-            }
-        }
-        if (done_packed) {
-        } else if constexpr (KH > 0) {
-            for (int s0 = 0; s0 < steps; s0 += KH) {
-                if (s0 > 0) {
-                    refresh_halos<Real, P, NW, KH>(u, w, hx, buf, warp, lane);
-                    buf ^= 1;
-                }
-                const int s1 = (s0 + KH < steps) ? s0 + KH : steps;
-                for (int s = s0; s < s1; ++s) {
-                    Real lft, rgt;
-                    warp_neighbours<Real, P>(u, lft, rgt, lane);
-                    const int64_t n = n0 + s;
-                    if (has_probe) {
-                        if (few_probes) {
-                            if (pq0 >= 0) record_owned<Real, P>(u, lft, rgt, s_probes[pq0], wabs, tb, n);
-                            if (pq1 >= 0) record_owned<Real, P>(u, lft, rgt, s_probes[pq1], wabs, tb, n);
-                        } else {
-                            record_probes<Real, P>(u, lft, rgt, wabs, tb, own_lo, own_hi, td.probe_begin,
-                                                   td.probe_end, prm.probes, n);
-                        }
-                    }
-                    if (special) {
-                        Real uold_s = Real(0), sval = Real(0);
-                        if (sp.rs >= 0) {
-                            sval = pr.src[(n + 1) * pr.src_stride];
-                            if constexpr (FORM == kIncrement) uold_s = select_reg<Real, P>(u, sp.rs);
-                        }
-                        const Real fa_old = pr.fA ? pr.fA[n] : Real(0);
-                        const Real fa_new = pr.fA ? pr.fA[n + 1] : Real(0);
-                        const Real fb_old = pr.fB ? pr.fB[n] : Real(0);
-                        const Real fb_new = pr.fB ? pr.fB[n + 1] : Real(0);
-                        leap_step<Real, FORM, P>(u, w, lft, rgt, c2, kk);
-                        patch_special<Real, FORM, P>(u, w, sp, uold_s, sval, fa_old, fa_new, fb_old, fb_new);
-                    } else {
-                        leap_step<Real, FORM, P>(u, w, lft, rgt, c2, kk);
-                    }
-                }
-            }
-        } else if (!slow && !has_probe) {
-            // interior tile: halo latency hidden behind the interior updates
-            for (int s = 0; s < steps; ++s) {
-                split_step<Real, FORM, P, NW>(u, w, c2, kk, xch, buf, warp, lane);
-                buf ^= 1;
-            }
-        } else
-        for (int s = 0; s < steps; ++s) {
-            Real lft, rgt;
-            exchange<Real, P, NW>(u, lft, rgt, xch, buf, warp, lane);
-            buf ^= 1;
-            const int64_t n = n0 + s;
-            if (has_probe) {
-                if (few_probes) {
-                    if (pq0 >= 0) record_owned<Real, P>(u, lft, rgt, s_probes[pq0], wabs, tb, n);
-                    if (pq1 >= 0) record_owned<Real, P>(u, lft, rgt, s_probes[pq1], wabs, tb, n);
-                } else {
-                    record_probes<Real, P>(u, lft, rgt, wabs, tb, 0, P, td.probe_begin, td.probe_end, prm.probes, n);
-                }
-            }
-            if (special) {
-                Real uold_s = Real(0), sval = Real(0);
-                if (sp.rs >= 0) {
-                    sval = pr.src[(n + 1) * pr.src_stride];
-                    if constexpr (FORM == kIncrement) uold_s = select_reg<Real, P>(u, sp.rs);
-                }
-                const Real fa_old = pr.fA ? pr.fA[n] : Real(0);
-                const Real fa_new = pr.fA ? pr.fA[n + 1] : Real(0);
-                const Real fb_old = pr.fB ? pr.fB[n] : Real(0);
-                const Real fb_new = pr.fB ? pr.fB[n + 1] : Real(0);
-                leap_step<Real, FORM, P>(u, w, lft, rgt, c2, kk);
-                patch_special<Real, FORM, P>(u, w, sp, uold_s, sval, fa_old, fa_new, fb_old, fb_new);
-            } else {
-                leap_step<Real, FORM, P>(u, w, lft, rgt, c2, kk);
-            }
-        }
+        predict_tile<Real, FORM, P, NW, KH, PK, 0>(prm, pr, td, u, w, gj0, n0, steps, tb, own_lo, own_hi, s_probes,
+                                                  np, xch, hx, warp, lane, edge);
 
         // ---- select + update: write the window back, store only the core
         __syncthreads();  // every thread has read its window (KH > 0: windows overlap)
@@ -396,6 +460,224 @@ __global__ void __launch_bounds__(NT, MINB) span_kernel(const __grid_constant__ 
     }
 }
 
+// ---- warp-specialised span kernel --------------------------------------------
+// NT compute threads (NT/32 warps) and one producer warp.  Lane 0 of the
+// producer warp takes the tickets, waits for the neighbour flags, fills the
+// stages with TMA loads, stores the finished cores and publishes the flags;
+// the compute warps only wait for a full stage, run the span and hand the
+// stage back.
+//
+// Stage y (two of them) cycles through: producer arms full_bar[y] (a TMA load
+// with its transaction bytes, or a plain arrival with ticket -1 = stop) ->
+// compute warps wait full_bar[y], copy their windows to registers and arrive on
+// read_bar[y] -> step -> wait read_bar[y] (every warp has read the stage; in
+// practice long complete), write their owned points back, fence the async
+// proxy and arrive on empty_bar[y] (one arrival per warp) -> producer waits
+// empty_bar[y], bulk-stores the core, waits for the store to complete and
+// publishes the tile; only then is stage y armed again.  The stage's ticket,
+// tile geometry, a copy of its problem record and its probe table sit beside
+// the stage and are written only while the stage belongs to the producer.
+//
+// With free warp windows (no data exchange between warps inside a span) the
+// compute warps share no barrier at all: each warp decides on its own to stop.
+// Variants that exchange halos between warps (KH = 0, or refreshed warp halos)
+// take one decision for all compute threads at a named barrier (barrier 1,
+// which the producer never joins) so that their per-step barriers stay uniform.
+
+template <typename Real>
+struct StageInfo {
+    ProblemDev<Real> pr;  // copy of the tile's problem record
+    TileDev td;
+    long long ticket;     // -1: no more work
+    int64_t gj0;          // problem coordinate of the window start
+    int64_t n0;           // first level of the span
+    int k;                // span
+    int tile;
+    int np;               // probes of the tile (staged when np <= kTileProbes)
+    int steps;            // steps of this span
+    int edge;             // the window touches a physical boundary
+    int pad_;
+};
+
+template <typename Real, int W>
+__device__ void producer_loop(const SpanParams<Real>& prm, Real* stage, uint64_t* full_bar, uint64_t* empty_bar,
+                              StageInfo<Real>* info, ProbeDev<Real> (*sprobes)[kTileProbes])
+{
+    int it = 0;
+    uint32_t fpar = 0u;   // bit y: parity of the next phase of full_bar[y] the producer arms
+    uint32_t epar = 0u;   // bit y: parity of the next phase of empty_bar[y]
+    uint32_t armed = 0u;  // bit y: full_bar[y] has been armed at least once
+
+    auto arm = [&](int y, long long t) {
+        StageInfo<Real>& si = info[y];
+        si.ticket = t;
+        if (t >= 0) {
+            const int tile = (int)(t % prm.ntiles);
+            const int k = (int)(t / prm.ntiles);
+            const TileDev td = prm.tiles[tile];
+            const ProblemDev<Real> pr = prm.problems[td.problem];
+            const int np = td.probe_end - td.probe_begin;
+            const int64_t gj0 = (int64_t)td.local * prm.core - prm.H;
+            const int64_t n0 = (int64_t)k * prm.S;
+            si.pr = pr;
+            si.td = td;
+            si.gj0 = gj0;
+            si.n0 = n0;
+            si.k = k;
+            si.tile = tile;
+            si.np = np;
+            si.steps = (int)((prm.T - n0 < prm.S) ? (prm.T - n0) : prm.S);
+            si.edge = (gj0 <= 0) || (gj0 + W - 1 >= pr.nx - 1);
+            if (np > 0 && np <= kTileProbes)
+                for (int q = 0; q < np; ++q) sprobes[y][q] = prm.probes[td.probe_begin + q];
+            issue_load<Real, W>(prm, t, stage + y * 2 * W, &full_bar[y]);
+        } else {
+            mbar_arrive(&full_bar[y]);
+        }
+        fpar ^= 1u << y;
+        armed |= 1u << y;
+    };
+
+    int y = 0;
+    long long t = grab_ticket(prm, it++);
+    if (t >= 0 && !wait_deps(prm, t)) t = -1;
+    arm(0, t);
+    while (t >= 0) {
+        // prefetch the next ticket into the other stage when its neighbours are done
+        const long long tn = grab_ticket(prm, it++);
+        bool next_armed = false;
+        if (tn < 0 || deps_ready(prm, tn)) {
+            arm(y ^ 1, tn);
+            next_armed = true;
+        }
+        // the compute warps hand stage y back
+        if (!mbar_wait_backoff(&empty_bar[y], (epar >> y) & 1u, prm.wait_ns, &prm.err->code)) {
+            latch_error(prm.err, kDevTimeoutLoad, (int)(t % prm.ntiles), (int)(t / prm.ntiles), 0);
+            if (!next_armed) arm(y ^ 1, -1);
+            break;
+        }
+        epar ^= 1u << y;
+        // select + update: store the core, publish once the store has landed
+        {
+            const StageInfo<Real>& si = info[y];
+            const int64_t dst = si.pr.base + (int64_t)si.td.local * prm.core;
+            const uint32_t bytes = (uint32_t)prm.core * sizeof(Real);
+            const int b = (si.k + 1) & 1;
+            Real* su = stage + y * 2 * W;
+            bulk_store(prm.q0[b] + dst, su + prm.H, bytes);
+            bulk_store(prm.q1[b] + dst, su + W + prm.H, bytes);
+            bulk_commit();
+            bulk_wait_all();
+            publish(prm, t);
+        }
+        if (!next_armed) {
+            // the next ticket may need the tile just published
+            if (wait_deps(prm, tn)) {
+                arm(y ^ 1, tn);
+            } else {
+                arm(y ^ 1, -1);
+                break;
+            }
+        }
+        t = tn;
+        y ^= 1;
+    }
+    bulk_wait_all();
+    // let every armed phase complete (a load in flight) before shared memory is released
+    for (int st = 0; st < 2; ++st)
+        if ((armed >> st) & 1u)
+            mbar_wait_bounded(&full_bar[st], ((fpar >> st) & 1u) ^ 1u, prm.wait_ns, nullptr);
+}
+
+template <typename Real, int FORM, int P, int NT, int KH, int MINB>
+__global__ void __launch_bounds__(NT + 32, MINB) span_kernel_ws(const __grid_constant__ SpanParams<Real> prm)
+{
+    using G = Geom<P, NT, KH>;
+    constexpr int W = G::W;
+    constexpr int NW = G::NW;
+    constexpr bool kFree = G::FREE;
+    static_assert(W % 4 == 0, "windows must span whole 16-byte units");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Real* stage = reinterpret_cast<Real*>(smem_raw);  // [2 stages][2 components][W]
+    Real* xch = stage + 4 * W;
+    Real* hx = xch + ((4 * NW + 15) / 16) * 16;
+    __shared__ __align__(8) uint64_t full_bar[2];
+    __shared__ __align__(8) uint64_t empty_bar[2];
+    __shared__ __align__(8) uint64_t read_bar[2];
+    __shared__ __align__(16) StageInfo<Real> s_info[2];
+    __shared__ ProbeDev<Real> s_probes[2][kTileProbes];
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+
+    if (tid == NT) {
+        mbar_init(&full_bar[0], 1);
+        mbar_init(&full_bar[1], 1);
+        mbar_init(&empty_bar[0], NW);
+        mbar_init(&empty_bar[1], NW);
+        mbar_init(&read_bar[0], NW);
+        mbar_init(&read_bar[1], NW);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async_smem();
+    }
+    __syncthreads();  // the last CTA-wide barrier: from here on only barrier 1 (compute threads)
+
+    if (warp == NW) {
+        if (lane == 0) producer_loop<Real, W>(prm, stage, full_bar, empty_bar, s_info, s_probes);
+        return;
+    }
+
+    const int tb = warp * G::CW + lane * P;  // window index of the thread's first point
+    int own_lo, own_hi;
+    owned_range<P, NW, KH>(warp, lane, own_lo, own_hi);
+    uint32_t fpar = 0u, rpar = 0u;
+    int y = 0;
+    for (;;) {
+        const bool ok = mbar_wait_bounded(&full_bar[y], (fpar >> y) & 1u, prm.wait_ns, &prm.err->code);
+        fpar ^= 1u << y;
+        Real* su = stage + y * 2 * W;
+        Real* sw = su + W;
+        Real u[P], w[P];
+        smem_to_regs<Real, P>(su + tb, u);
+        smem_to_regs<Real, P>(sw + tb, w);
+        if (!ok) latch_error(prm.err, kDevTimeoutLoad, -1, -1, 0);
+        if constexpr (kFree) {
+            // this warp's decision; its window is in registers
+            if (__any_sync(kFull, !ok)) break;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&read_bar[y]);
+        } else {
+            // one decision for all compute threads; after this barrier stage y is only written
+            if (block_sync_or<NT>(!ok)) break;
+        }
+        const StageInfo<Real>& si = s_info[y];
+        if (si.ticket < 0) break;
+
+        const int steps = si.steps;
+        if (kFree && steps > KH) {
+            // the host never schedules a span longer than a free variant's warp halo
+            if (tid == 0) latch_error(prm.err, kDevBadTicket, si.tile, si.k, 0);
+        } else {
+            predict_tile<Real, FORM, P, NW, KH, 0, NT>(prm, si.pr, si.td, u, w, si.gj0, si.n0, steps, tb, own_lo,
+                                                       own_hi, s_probes[y], si.np, xch, hx, warp, lane,
+                                                       si.edge != 0);
+        }
+        if constexpr (kFree) {
+            // every warp has read its window from stage y before anyone overwrites it
+            const bool rd = mbar_wait_bounded(&read_bar[y], (rpar >> y) & 1u, prm.wait_ns, &prm.err->code);
+            if (!rd) latch_error(prm.err, kDevTimeoutLoad, si.tile, si.k, 0);
+        }
+        rpar ^= 1u << y;
+        owned_to_smem<Real, P, KH>(su + tb, u, own_lo, own_hi);
+        owned_to_smem<Real, P, KH>(sw + tb, w, own_lo, own_hi);
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty_bar[y]);
+        y ^= 1;
+    }
+}
+
 // ---- variant registry ------------------------------------------------------
 
 namespace {
@@ -413,14 +695,26 @@ Entry make_entry()
 {
     using G = Geom<P, NT, KH>;
     Entry e;
-    e.info = VariantInfo{sizeof(Real) == 8 ? kF64 : kF32, FORM, P, NT, KH, G::W};
+    e.info = VariantInfo{sizeof(Real) == 8 ? kF64 : kF32, FORM, P, NT, KH, G::W, NT, 0};
     e.fn = reinterpret_cast<const void*>(&span_kernel<Real, FORM, P, NT, KH, PK, MINB>);
     e.smem = sizeof(Real) * (4 * G::W + G::XCH);
     return e;
 }
 
-// The first entry of each dtype/form is its default (the fastest measured on
-// the c2 workload); the autotuner times them all.
+// Warp-specialised variants: NT compute threads + one producer warp.
+template <typename Real, int FORM, int P, int NT, int KH, int MINB>
+Entry make_entry_ws()
+{
+    using G = Geom<P, NT, KH>;
+    Entry e;
+    e.info = VariantInfo{sizeof(Real) == 8 ? kF64 : kF32, FORM, P, NT, KH, G::W, NT + 32, G::FREE ? KH : 0};
+    e.fn = reinterpret_cast<const void*>(&span_kernel_ws<Real, FORM, P, NT, KH, MINB>);
+    e.smem = sizeof(Real) * (4 * G::W + G::XCH);
+    return e;
+}
+
+// The first entry of each dtype/form that accepts the plan's span is its
+// default (the fastest measured on the c2 workload); the autotuner times them all.
 const Entry* table(int* n)
 {
     static const Entry entries[] = {
@@ -437,6 +731,12 @@ const Entry* table(int* n)
         make_entry<double, kCanonical, 16, 256, 0, 0, 1>(),
         make_entry<double, kCanonical, 8, 256, 4, 0, 2>(),
         make_entry<double, kIncrement, 8, 256, 0, 0, 2>(),
+        make_entry_ws<float, kIncrement, 16, 128, 32, 5>(),
+        make_entry_ws<float, kIncrement, 16, 128, 16, 5>(),
+        make_entry_ws<float, kIncrement, 16, 128, 8, 5>(),
+        make_entry_ws<float, kIncrement, 16, 256, 32, 3>(),
+        make_entry_ws<double, kCanonical, 8, 128, 0, 4>(),
+        make_entry_ws<double, kCanonical, 8, 256, 0, 2>(),
     };
     *n = (int)(sizeof(entries) / sizeof(entries[0]));
     return entries;
@@ -477,7 +777,7 @@ cudaError_t span_occupancy(int v, int* blocks_per_sm)
     const Entry& e = table(&n)[v];
     cudaError_t st = span_prepare(v);
     if (st != cudaSuccess) return st;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, e.fn, e.info.NT, e.smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, e.fn, e.info.threads, e.smem);
 }
 
 cudaError_t span_launch(int v, const void* params, int grid, cudaStream_t s)
@@ -485,7 +785,7 @@ cudaError_t span_launch(int v, const void* params, int grid, cudaStream_t s)
     int n;
     const Entry& e = table(&n)[v];
     void* args[] = {const_cast<void*>(params)};
-    return cudaLaunchKernel(e.fn, dim3(grid), dim3(e.info.NT), args, e.smem, s);
+    return cudaLaunchKernel(e.fn, dim3(grid), dim3(e.info.threads), args, e.smem, s);
 }
 
 }  // namespace rswr

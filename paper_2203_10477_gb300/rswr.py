@@ -99,6 +99,8 @@ SIGNATURES = {
     "rswr_variant_count": (_i32, []),
     "rswr_variant_get": (_st, [_i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                                ctypes.POINTER(_i32)]),
+    "rswr_variant_get_tiling": (_st, [_i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                      ctypes.POINTER(_i32)]),
 }
 
 _lib: Optional[ctypes.CDLL] = None
@@ -170,7 +172,10 @@ def variants() -> list[dict]:
     for v in range(lib().rswr_variant_count()):
         d, f, p, n = _i32(), _i32(), _i32(), _i32()
         check(lib().rswr_variant_get(v, ctypes.byref(d), ctypes.byref(f), ctypes.byref(p), ctypes.byref(n)))
-        out.append({"variant": v, "dtype": d.value, "form": f.value, "P": p.value, "NT": n.value})
+        kh, w, ms, th = _i32(), _i32(), _i32(), _i32()
+        check(lib().rswr_variant_get_tiling(v, ctypes.byref(kh), ctypes.byref(w), ctypes.byref(ms), ctypes.byref(th)))
+        out.append({"variant": v, "dtype": d.value, "form": f.value, "P": p.value, "NT": n.value,
+                    "KH": kh.value, "window": w.value, "max_span": ms.value, "threads": th.value})
     return out
 
 

@@ -136,21 +136,52 @@ def test_every_variant_and_span_gives_identical_bits(R, oracle_mod, dtype, form)
     fA = inputs.gaussian_pulse(T, dt, sigma_steps=15)
     q0 = inputs.smooth_random_state(nx, seed=3)
     dt_ = np.float64 if dtype == F64 else np.float32
+    jr = 12345
     ref = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, np.zeros(T + 1), form=ORACLE_FORM[form], prec=prec(dtype),
+                              q0=q0.astype(dt_), rec_j=[jr])
+    rs = oracle_mod.rswr_mask(nx, T, 1.0, dt, fA, np.zeros(T + 1), N, ov, form=ORACLE_FORM[form], prec=prec(dtype),
                               q0=q0.astype(dt_))
     plan = R.Plan(0.0, 1.0, 1.0, nx, dt, N, ov, dtype=dtype, form=form)
     vs = [v for v in R.variants() if v["dtype"] == dtype and v["form"] == form]
     assert len(vs) >= 2
     for v in vs:
-        plan.set_variant(v["variant"])
-        for S in (1, 7, ov // 2):
+        for S in (1, 7, 16, ov // 2):
+            if v["max_span"] and S > v["max_span"]:
+                continue
             plan.set_span(S)
+            plan.set_variant(v["variant"])
+            assert plan.info()["variant"] == v["variant"] and plan.info()["span_steps"] == S
             for mode in (0, 1):
                 plan.set_mode(mode)
-                out = plan.run(fA, None, T, q0=q0)
+                out = plan.run(fA, None, T, q0=q0, traces=True, j_r=jr)
                 plan.check()
-                assert_bitwise(host(out["u"]), ref["u"], f"variant {v} S={S} mode={mode}")
-                assert_bitwise(host(out["w"]), ref["w"], f"variant {v} S={S} mode={mode}")
+                what = f"variant {v} S={S} mode={mode}"
+                assert_bitwise(host(out["u"]), ref["u"], what)
+                assert_bitwise(host(out["w"]), ref["w"], what)
+                assert_bitwise(host(out["recv"]), ref["rec"][0], what + " receiver")
+                assert_bitwise(host(out["traces"]), rs["traces"], what + " traces")
+
+
+def test_span_limit_of_free_warp_windows(R):
+    """A variant whose warp halo is shorter than the span is refused; set_span
+    moves a plan off such a variant onto one that runs the span."""
+    free = [v for v in R.variants() if v["max_span"] > 0]
+    assert free, "no free-window variant registered"
+    v = free[0]
+    m = v["max_span"]
+    nx = 40001
+    plan = R.Plan(0.0, 1.0, 1.0, nx, 0.9 / (nx - 1), 4, 2 * m + 16, dtype=v["dtype"], form=v["form"])
+    plan.set_span(m)
+    plan.set_variant(v["variant"])
+    assert plan.info()["variant"] == v["variant"]
+    plan.set_span(m + 8)
+    info = plan.info()
+    assert info["span_steps"] == m + 8 and info["variant"] != v["variant"]
+    other = R.variants()[info["variant"]]
+    assert other["max_span"] == 0 or other["max_span"] >= m + 8
+    with pytest.raises(R.RSWRError):
+        plan.set_variant(v["variant"])
+    assert plan.info()["variant"] == info["variant"]
 
 
 @pytest.mark.parametrize("T", [0, 1, 5, 31, 32, 33])
