@@ -438,116 +438,5 @@ __device__ __forceinline__ void owned_to_smem(Real* s, const Real (&r)[P], int o
     }
 }
 
-// ---- packed FP32 (sm_100+ f32x2): two points per instruction ----------------
-// A thread's P points are two half blocks A = [0, P/2) and B = [P/2, P); pair i
-// holds (A[i], B[i]) in one 64-bit register, so a pair's neighbours are pairs
-// i-1 and i+1 and every packed operation is, lane by lane, the scalar one.
-
-__device__ __forceinline__ uint64_t pk2(float lo, float hi)
-{
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ float lo2(uint64_t v)
-{
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-    return lo;
-}
-__device__ __forceinline__ float hi2(uint64_t v)
-{
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-    return hi;
-}
-__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b)
-{
-    uint64_t r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b)
-{
-    uint64_t r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c)
-{
-    uint64_t r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-
-// Point j of a thread in the packed layout.
-template <int P>
-__device__ __forceinline__ float pget(const uint64_t (&U)[P / 2], int j)
-{
-    return j < P / 2 ? lo2(U[j]) : hi2(U[j - P / 2]);
-}
-
-// `steps` increment-form leapfrog steps of one thread's P points held packed,
-// with warp halos of KH points refreshed every KH steps (as refresh_halos).
-// Interior tiles only: no Dirichlet nodes, sources or probes.
-template <int P, int NW, int KH>
-__device__ __forceinline__ void packed_increment_steps(float (&u)[P], float (&w)[P], float c2, int steps, float* hx,
-                                                       int& buf, int warp, int lane)
-{
-    constexpr int H2 = P / 2;
-    static_assert(P % 2 == 0 && H2 >= 2, "packed layout needs an even number of points");
-    uint64_t U[H2], V[H2];
-#pragma unroll
-    for (int i = 0; i < H2; ++i) {
-        U[i] = pk2(u[i], u[H2 + i]);
-        V[i] = pk2(w[i], w[H2 + i]);
-    }
-    const uint64_t c2p = pk2(c2, c2);
-    for (int s0 = 0; s0 < steps; s0 += KH) {
-        if (s0 > 0) {
-            // unpack the halo-relevant points, refresh, repack (KH <= P/2 points per side)
-#pragma unroll
-            for (int i = 0; i < H2; ++i) {
-                u[i] = lo2(U[i]);
-                u[H2 + i] = hi2(U[i]);
-                w[i] = lo2(V[i]);
-                w[H2 + i] = hi2(V[i]);
-            }
-            refresh_halos<float, P, NW, KH>(u, w, hx, buf, warp, lane);
-            buf ^= 1;
-#pragma unroll
-            for (int i = 0; i < H2; ++i) {
-                U[i] = pk2(u[i], u[H2 + i]);
-                V[i] = pk2(w[i], w[H2 + i]);
-            }
-        }
-        const int s1 = (s0 + KH < steps) ? s0 + KH : steps;
-        for (int s = s0; s < s1; ++s) {
-            float lft = __shfl_up_sync(kFull, hi2(U[H2 - 1]), 1);  // previous thread's last point
-            float rgt = __shfl_down_sync(kFull, lo2(U[0]), 1);     // next thread's first point
-            if (lane == 0) lft = lo2(U[1]);                         // mirror at the warp window ends
-            if (lane == 31) rgt = hi2(U[H2 - 2]);
-            const uint64_t Lp = pk2(lft, lo2(U[H2 - 1]));  // left neighbours of pair 0
-            const uint64_t Rp = pk2(hi2(U[0]), rgt);       // right neighbours of pair H2-1
-            uint64_t dprev = sub2(U[0], Lp);
-#pragma unroll
-            for (int i = 0; i < H2; ++i) {
-                const uint64_t d = sub2(i < H2 - 1 ? U[i + 1] : Rp, U[i]);
-                const uint64_t v = fma2(c2p, sub2(d, dprev), V[i]);
-                dprev = d;
-                V[i] = v;
-                U[i] = add2(U[i], v);
-            }
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < H2; ++i) {
-        u[i] = lo2(U[i]);
-        u[H2 + i] = hi2(U[i]);
-        w[i] = lo2(V[i]);
-        w[H2 + i] = hi2(V[i]);
-    }
-}
-
 }  // namespace span
 }  // namespace rswr

@@ -143,7 +143,7 @@ struct Geom {
 // the window take it together.  The step loop is instantiated four times
 // (probes yes/no x special points yes/no) so that a plain interior tile runs
 // the bare stencil with no per-step tests.
-template <typename Real, int FORM, int P, int NW, int KH, int PK, int BAR>
+template <typename Real, int FORM, int P, int NW, int KH, int BAR>
 __device__ __forceinline__ void predict_tile(const SpanParams<Real>& prm, const ProblemDev<Real>& pr,
                                              const TileDev& td, Real (&u)[P], Real (&w)[P], int64_t gj0, int64_t n0,
                                              int steps, int tb, int own_lo, int own_hi,
@@ -253,12 +253,6 @@ __device__ __forceinline__ void predict_tile(const SpanParams<Real>& prm, const 
     };
 
     if constexpr (KH > 0) {
-        if constexpr (PK && FORM == kIncrement && sizeof(Real) == 4 && P >= 2 * KH) {
-            if (!slow && !has_probe) {
-                packed_increment_steps<P, NW, KH>(u, w, c2, steps, hx, buf, warp, lane);
-                return;
-            }
-        }
         if constexpr (P >= 2 * KH) {
             // warp halos refreshed every KH steps
             for (int s0 = 0; s0 < steps; s0 += KH) {
@@ -300,7 +294,7 @@ __device__ __forceinline__ void owned_range(int warp, int lane, int& own_lo, int
     own_hi = b < 0 ? 0 : (b > P ? P : b);
 }
 
-template <typename Real, int FORM, int P, int NT, int KH, int PK, int MINB>
+template <typename Real, int FORM, int P, int NT, int KH, int MINB>
 __global__ void __launch_bounds__(NT, MINB) span_kernel(const __grid_constant__ SpanParams<Real> prm)
 {
     using G = Geom<P, NT, KH>;
@@ -408,7 +402,7 @@ __global__ void __launch_bounds__(NT, MINB) span_kernel(const __grid_constant__ 
             __syncthreads();
         }
 
-        predict_tile<Real, FORM, P, NW, KH, PK, 0>(prm, pr, td, u, w, gj0, n0, steps, tb, own_lo, own_hi, s_probes,
+        predict_tile<Real, FORM, P, NW, KH, 0>(prm, pr, td, u, w, gj0, n0, steps, tb, own_lo, own_hi, s_probes,
                                                   np, xch, hx, warp, lane, edge);
 
         // ---- select + update: write the window back, store only the core
@@ -659,7 +653,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) span_kernel_ws(const __grid_con
             // the host never schedules a span longer than a free variant's warp halo
             if (tid == 0) latch_error(prm.err, kDevBadTicket, si.tile, si.k, 0);
         } else {
-            predict_tile<Real, FORM, P, NW, KH, 0, NT>(prm, si.pr, si.td, u, w, si.gj0, si.n0, steps, tb, own_lo,
+            predict_tile<Real, FORM, P, NW, KH, NT>(prm, si.pr, si.td, u, w, si.gj0, si.n0, steps, tb, own_lo,
                                                        own_hi, s_probes[y], si.np, xch, hx, warp, lane,
                                                        si.edge != 0);
         }
@@ -688,15 +682,14 @@ struct Entry {
     size_t smem;
 };
 
-// PK: packed FP32 pairs on interior tiles; MINB: CTAs per SM the register
-// allocation must allow.
-template <typename Real, int FORM, int P, int NT, int KH, int PK = 0, int MINB = 2>
+// MINB: CTAs per SM the register allocation must allow.
+template <typename Real, int FORM, int P, int NT, int KH, int MINB = 2>
 Entry make_entry()
 {
     using G = Geom<P, NT, KH>;
     Entry e;
     e.info = VariantInfo{sizeof(Real) == 8 ? kF64 : kF32, FORM, P, NT, KH, G::W, NT, 0};
-    e.fn = reinterpret_cast<const void*>(&span_kernel<Real, FORM, P, NT, KH, PK, MINB>);
+    e.fn = reinterpret_cast<const void*>(&span_kernel<Real, FORM, P, NT, KH, MINB>);
     e.smem = sizeof(Real) * (4 * G::W + G::XCH);
     return e;
 }
@@ -718,25 +711,24 @@ Entry make_entry_ws()
 const Entry* table(int* n)
 {
     static const Entry entries[] = {
-        make_entry<float, kIncrement, 16, 128, 8, 0, 4>(),
-        make_entry<float, kIncrement, 16, 128, 8, 0, 6>(),
-        make_entry<float, kIncrement, 16, 128, 8, 1, 4>(),
-        make_entry<float, kIncrement, 16, 128, 4, 0, 4>(),
-        make_entry<float, kIncrement, 16, 128, 0, 0, 4>(),
-        make_entry<float, kIncrement, 16, 256, 0, 0, 2>(),
-        make_entry<float, kIncrement, 8, 256, 0, 0, 3>(),
-        make_entry<float, kCanonical, 16, 128, 0, 0, 4>(),
-        make_entry<double, kCanonical, 8, 256, 0, 0, 2>(),
-        make_entry<double, kCanonical, 8, 128, 0, 0, 4>(),
-        make_entry<double, kCanonical, 16, 256, 0, 0, 1>(),
-        make_entry<double, kCanonical, 8, 256, 4, 0, 2>(),
-        make_entry<double, kIncrement, 8, 256, 0, 0, 2>(),
+        // FP32 increment (the FP32 default form)
+        make_entry_ws<float, kIncrement, 24, 128, 32, 4>(),  // free warp windows, spans <= 32
+        make_entry_ws<float, kIncrement, 28, 128, 32, 4>(),
         make_entry_ws<float, kIncrement, 16, 128, 32, 5>(),
+        make_entry_ws<float, kIncrement, 24, 128, 16, 4>(),  // spans <= 16
         make_entry_ws<float, kIncrement, 16, 128, 16, 5>(),
-        make_entry_ws<float, kIncrement, 16, 128, 8, 5>(),
-        make_entry_ws<float, kIncrement, 16, 256, 32, 3>(),
+        make_entry_ws<float, kIncrement, 16, 128, 8, 5>(),   // refreshed warp halos: any span
+        make_entry<float, kIncrement, 16, 128, 8, 4>(),
+        make_entry<float, kIncrement, 16, 128, 0, 4>(),
+        // FP32 canonical
+        make_entry<float, kCanonical, 16, 128, 0, 4>(),
+        // FP64 canonical (the FP64 default form)
         make_entry_ws<double, kCanonical, 8, 128, 0, 4>(),
         make_entry_ws<double, kCanonical, 8, 256, 0, 2>(),
+        make_entry<double, kCanonical, 8, 128, 0, 4>(),
+        make_entry<double, kCanonical, 8, 256, 0, 2>(),
+        // FP64 increment
+        make_entry<double, kIncrement, 8, 256, 0, 2>(),
     };
     *n = (int)(sizeof(entries) / sizeof(entries[0]));
     return entries;
