@@ -324,6 +324,20 @@ def profile_case(which: str, variant=None, span=None, full=False) -> None:
     from paper_2203_10477_gb300 import build, rswr
 
     build.build()
+    if which in ("adj64", "adj32"):
+        # the c4 gradient workload (dL/dfA and dL/da), run twice
+        p = inputs.c4(j_r=4000)
+        dtype = rswr.F64 if which == "adj64" else rswr.F32
+        td = torch.float64 if dtype == rswr.F64 else torch.float32
+        plan = rswr.Plan.from_problem(p, dtype=dtype)
+        fA = torch.as_tensor(p.fA, device="cuda").to(td)
+        w = torch.as_tensor(inputs.lowpass_noise(p.T, seed=4), device="cuda").to(td)
+        for _ in range(2):
+            plan.adjoint(fA, None, p.T, 4000, w, want_a=True)
+        torch.cuda.synchronize()
+        plan.check()
+        print(json.dumps({"profile_case": which, "nx": p.nx, "T": p.T, "info": plan.info()}))
+        return
     if full:
         p = inputs.c2()
     else:
@@ -436,6 +450,46 @@ def bench_large(torch, dev):
             "unit": UNIT, "ms_per_run": ms[0], "variant": info["variant"], "span_steps": info["span_steps"]}
 
 
+def bench_c5_batch(torch, rank, world, dist, dev):
+    """c5, second part: 512 uneven problems (nx in [2^12, 2^20], a in [0.5, 2],
+    CFL 0.9, overlap 64, 2^15 steps) in one persistent launch, FP32: the forward
+    run and the adjoint sweep that gives every problem's boundary-waveform
+    gradient for a smooth receiver cotangent.  Problems sharded across ranks."""
+    from paper_2203_10477_gb300 import rswr
+    from paper_2203_10477_gb300.shard import max_over_ranks, shard_problems, sum_over_ranks
+
+    probs = inputs.c5_uneven()
+    T = probs[0].T
+    idx = shard_problems([q.nx for q in probs], rank, world)
+    mine = [probs[i] for i in idx]
+    b = rswr.Batch(mine, dtype=rswr.F32, device=dev)
+    b.autotune(64)
+    fA = torch.as_tensor(np.concatenate([q.fA for q in mine]), device=dev).to(torch.float32)
+    n = int(b.offsets[-1])
+    out = (torch.empty(n, dtype=torch.float32, device=dev), torch.empty(n, dtype=torch.float32, device=dev))
+    run = lambda: b.run(fA, None, T, out=out)
+    run()
+    ms_f = _time(torch, run, 1)[0]
+    b.check()
+    jr = [q.meta["j_r"] for q in mine]
+    wbar = torch.as_tensor(np.stack([inputs.lowpass_noise(T, seed=1000 + i) for i in idx]), device=dev).to(torch.float32)
+    adj = lambda: b.adjoint(fA, None, T, jr, wbar)
+    adj()
+    ms_a = _time(torch, adj, 1)[0]
+    b.check()
+    info = b.info()
+    lups = float(sum((q.nx - 2) * T for q in mine))
+    t_f, t_a = max_over_ranks([ms_f / 1e3, ms_a / 1e3], dist, dev)
+    tot = sum_over_ranks([lups], dist, dev)[0]
+    del out, wbar
+    return {"workload": "c5: 512 uneven problems, nx U[2^12,2^20], a U[0.5,2], CFL 0.9, overlap 64, 2^15 steps, FP32",
+            "unit": UNIT, "lups_per_run": tot,
+            "forward": {"value": tot / t_f / 1e9, "ms_per_run": t_f * 1e3},
+            "adjoint_grad_fA": {"value": tot / t_a / 1e9, "ms_per_run": t_a * 1e3},
+            "variant": info["variant"], "span_steps": info["span_steps"], "mode": info["mode"],
+            "sharding": f"{world} rank(s), whole problems per rank"}
+
+
 def bench_paper_literal(torch, dev, T=2000):
     """The paper-literal RSWR (data-chosen spans, flux-exchange update) on the
     c2 grid (nx = 2^24, N = 1024, overlap 64, CFL 0.9) for 2000 steps."""
@@ -466,7 +520,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mono", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched / adjoint / large-grid measurements")
-    ap.add_argument("--profile-case", choices=["f64", "f32"], default=None,
+    ap.add_argument("--profile-case", choices=["f64", "f32", "adj64", "adj32"], default=None,
                     help="run the small profiling case (nx=2^22, 320 steps) twice and exit (for ncu)")
     ap.add_argument("--variant", type=int, default=None, help="kernel variant of the profiling case")
     ap.add_argument("--span", type=int, default=None, help="steps per span of the profiling case")
@@ -620,6 +674,8 @@ def main():
         line["adjoint"] = bench_adjoint(torch, dev)
         torch.cuda.empty_cache()
         line["large_grid"] = bench_large(torch, dev)
+        torch.cuda.empty_cache()
+        line["large_batch"] = bench_c5_batch(torch, rank, world, dist, dev)
         torch.cuda.empty_cache()
         line["paper_literal"] = bench_paper_literal(torch, dev)
     if rank == 0 and not args.no_cpu_baseline:

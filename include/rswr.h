@@ -139,6 +139,12 @@ rswr_status rswr_plan_set_mode(rswr_plan_t plan, int32_t mode);
 /* Upper bound, in seconds, of every device-side wait (default 5 s). */
 rswr_status rswr_plan_set_wait_limit(rswr_plan_t plan, double seconds);
 
+/* Adjoint checkpoint spacing (rswr_adjoint with grad_a): a checkpoint every
+ * `spans` spans (1 keeps every span state; the whole adjoint sweep is then one
+ * persistent launch); 0 (default) chooses automatically.  RSWR_EINVAL for
+ * spans < 0. */
+rswr_status rswr_plan_set_checkpoint_spacing(rswr_plan_t plan, int64_t spans);
+
 /* Failure-injection hook for tests: in persistent mode, CTA tile `tile` does
  * not publish completion of span `span`, so its neighbours' bounded waits
  * expire and the run reports RSWR_ETIMEOUT.  tile = -1 disables. */
@@ -228,8 +234,12 @@ rswr_status rswr_mono(rswr_plan_t plan, const void* fA, const void* fB, int64_t 
  *   grad_a[0]  = dL/da       (one double, device pointer; NULL skips it).
  * The adjoint variables obey the leapfrog backward in time with zero
  * Dirichlet data and the source wbar at j_r; they run through the same span
- * kernel.  dL/da pairs them with the forward levels, recomputed from
- * span-boundary checkpoints (sqrt(#spans) of them) inside shared memory.
+ * kernel.  dL/da pairs them with the forward levels, recomputed inside
+ * shared memory from span-boundary states: by default every span state is kept
+ * when they fit in half of the free device memory (one forward sweep, then one
+ * persistent adjoint launch over all spans), else one checkpoint every
+ * ceil(sqrt(#spans)) spans with the states of each segment recomputed before
+ * its spans are processed (rswr_plan_set_checkpoint_spacing overrides).
  * Canonical plans give grad_fA bit-identical to a plain FP64 discrete adjoint
  * of the canonical leapfrog.
  */
@@ -264,6 +274,7 @@ rswr_status rswr_batch_get_info(rswr_batch_t batch, rswr_plan_info* info);
 rswr_status rswr_batch_set_mode(rswr_batch_t batch, int32_t mode);
 rswr_status rswr_batch_set_variant(rswr_batch_t batch, int32_t variant);
 rswr_status rswr_batch_set_wait_limit(rswr_batch_t batch, double seconds);
+rswr_status rswr_batch_set_checkpoint_spacing(rswr_batch_t batch, int64_t spans);
 rswr_status rswr_batch_set_kernel_events(rswr_batch_t batch, void* start, void* stop);
 rswr_status rswr_batch_set_graph(rswr_batch_t batch, int32_t enable);
 /* As rswr_plan_autotune, over the batch's own problems. */

@@ -48,6 +48,157 @@ __device__ __forceinline__ bool is_special(const Special& sp, int P)
     return sp.r0 >= 0 || sp.r1 >= 0 || sp.rs >= 0 || sp.rlo > 0 || sp.rhi < P - 1;
 }
 
+// Geometry and data of one adjoint tile.
+template <typename Real>
+struct AdjTile {
+    const ProblemDev<Real>* pu;  // forward problem
+    const ProblemDev<Real>* pl;  // adjoint problem
+    TileDev td;
+    int64_t gj0;                 // problem coordinate of the window start
+    int64_t n0, m0;              // first forward / adjoint level of the span
+    int len;                     // steps of the span
+};
+
+// One tile of the adjoint sweep on a staged window (stage[0..1]: the forward
+// pair at level n0, stage[2..3]: the adjoint pair at level m0; each thread reads
+// and writes only its own P points).  u phase: len forward levels recomputed in
+// registers, the Laplacian of each level to `laps`; lambda phase: the probes
+// (dL/dfA), the pairing with the Laplacians on the core, len adjoint steps.
+// The adjoint pair is written back to stage[2..3].  Returns this thread's part of
+// sum lambda^{n+1} lap(u^n).  BAR: the barrier of the window's threads; `buf`
+// (the exchange-slot parity) continues across calls so that consecutive
+// exchanges always alternate slots.
+template <typename Real, int FORM, int P, int NT, int SA, int BAR>
+__device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTile<Real>& at, Real* stage, Real* laps,
+                                         Real* xch, int& buf)
+{
+    constexpr int W = NT * P;
+    constexpr int NW = NT / 32;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const ProblemDev<Real>& pu = *at.pu;
+    const ProblemDev<Real>& pl = *at.pl;
+    const int64_t nx = pu.nx;
+    const int64_t gj0 = at.gj0;
+    const int64_t wabs = pu.base + gj0;
+    const int64_t gj = gj0 + (int64_t)tid * P;
+    const Real c2 = pu.c2, kk = pu.k;
+    const bool edge = (gj0 <= 0) || (gj0 + W - 1 >= nx - 1);
+    const bool has_src = pl.js >= 0 && pl.js >= gj0 && pl.js < gj0 + W;
+    const int len = at.len;
+
+    // ---- u phase: levels n0 .. n0+len-1, Laplacians of every level to shared memory
+    {
+        Real u[P], w[P];
+        smem_to_regs<Real, P>(stage + 0 * W + tid * P, u);
+        smem_to_regs<Real, P>(stage + 1 * W + tid * P, w);
+        const Special sp = special_points<Real, P>(gj, nx, -1);
+        const bool special = edge && is_special(sp, P);
+        for (int s = 0; s < len; ++s) {
+            Real lft, rgt;
+            exchange<Real, P, NW, BAR>(u, lft, rgt, xch, buf, warp, lane);
+            buf ^= 1;
+            Real* lp = laps + s * W + tid * P;
+            const bool step = s + 1 < len;
+            // one pass: the Laplacian of this level (from the step's own neighbour
+            // sum, (uL + uR) - 2u = fma(-2, u, uL + uR) exactly) and the step
+            if constexpr (FORM == kCanonical) {
+                Real ul = lft;
+#pragma unroll
+                for (int i = 0; i < P; ++i) {
+                    const Real uc = u[i];
+                    const Real ur = i < P - 1 ? u[i + 1] : rgt;
+                    const Real sum = radd(ul, ur);
+                    lp[i] = rfma(Real(-2), uc, sum);
+                    if (step) {
+                        u[i] = rfma(c2, sum, rfma(kk, uc, -w[i]));
+                        w[i] = uc;
+                    }
+                    ul = uc;
+                }
+            } else {
+                Real d_prev = rsub(u[0], lft);
+#pragma unroll
+                for (int i = 0; i < P; ++i) {
+                    const Real ur = i < P - 1 ? u[i + 1] : rgt;
+                    const Real d = rsub(ur, u[i]);
+                    const Real lap = rsub(d, d_prev);
+                    d_prev = d;
+                    lp[i] = lap;
+                    if (step) {
+                        const Real v = rfma(c2, lap, w[i]);
+                        w[i] = v;
+                        u[i] = radd(u[i], v);
+                    }
+                }
+            }
+            if (step && special) {
+                const int64_t n = at.n0 + s;
+                const Real fa_old = pu.fA ? pu.fA[n] : Real(0), fa_new = pu.fA ? pu.fA[n + 1] : Real(0);
+                const Real fb_old = pu.fB ? pu.fB[n] : Real(0), fb_new = pu.fB ? pu.fB[n + 1] : Real(0);
+                patch_special<Real, FORM, P>(u, w, sp, Real(0), Real(0), fa_old, fa_new, fb_old, fb_new);
+            }
+        }
+    }
+
+    // ---- lambda phase: levels m0 .. m0+len-1 pair with u levels n0+len-1 .. n0
+    Real racc = Real(0);
+    Real l[P], lw[P];
+    smem_to_regs<Real, P>(stage + 2 * W + tid * P, l);
+    smem_to_regs<Real, P>(stage + 3 * W + tid * P, lw);
+    const Special sp = special_points<Real, P>(gj, nx, has_src ? pl.js : -1);
+    const bool special = (edge || has_src) && is_special(sp, P);
+    // core points that are interior grid points: [jlo, jhi)
+    const int64_t core_lo = gj0 + prm.H, core_hi = core_lo + prm.core;
+    const int64_t jlo = core_lo > 1 ? core_lo : 1;
+    const int64_t jhi = core_hi < nx - 1 ? core_hi : nx - 1;
+    for (int s = 0; s < len; ++s) {
+        Real lft, rgt;
+        exchange<Real, P, NW, BAR>(l, lft, rgt, xch, buf, warp, lane);
+        buf ^= 1;
+        const int64_t m = at.m0 + s;
+        if (at.td.probe_end > at.td.probe_begin)
+            record_probes<Real, P>(l, lft, rgt, wabs, tid * P, 0, P, at.td.probe_begin, at.td.probe_end, prm.probes,
+                                   m);
+        // each thread reads the Laplacians of its own points only
+        const Real* lp = laps + (len - 1 - s) * W + tid * P;
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            const int64_t j = gj + i;
+            if (j >= jlo && j < jhi) racc = rfma(l[i], lp[i], racc);
+        }
+        if (special) {
+            const Real sval = sp.rs >= 0 ? pl.src[(m + 1) * pl.src_stride] : Real(0);
+            // the increment form adds the source to v before u' = u + v: keep u
+            const Real uold = (FORM == kIncrement && sp.rs >= 0) ? select_reg<Real, P>(l, sp.rs) : Real(0);
+            leap_step<Real, FORM, P>(l, lw, lft, rgt, c2, kk);
+            patch_special<Real, FORM, P>(l, lw, sp, uold, sval, Real(0), Real(0), Real(0), Real(0));
+        } else {
+            leap_step<Real, FORM, P>(l, lw, lft, rgt, c2, kk);
+        }
+    }
+    regs_to_smem<Real, P>(stage + 2 * W + tid * P, l);
+    regs_to_smem<Real, P>(stage + 3 * W + tid * P, lw);
+    return racc;
+}
+
+// Sum of racc over the window's threads in a fixed order (warp shuffles, then
+// the warps in order); the result is valid in thread 0.
+template <int NT, int BAR>
+__device__ __forceinline__ double block_sum(double acc, double* red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) red[warp] = acc;
+    block_sync<BAR>();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < NT / 32; ++q) t += red[q];
+    return t;
+}
+
 template <typename Real, int FORM, int P, int NT, int SA>
 __global__ void __launch_bounds__(NT) adjoint_kernel(const __grid_constant__ AdjParams<Real> prm)
 {
@@ -61,8 +212,6 @@ __global__ void __launch_bounds__(NT) adjoint_kernel(const __grid_constant__ Adj
     __shared__ double red[NW];
 
     const int tid = threadIdx.x;
-    const int lane = tid & 31;
-    const int warp = tid >> 5;
     if (tid == 0) {
         mbar_init(&bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -70,14 +219,18 @@ __global__ void __launch_bounds__(NT) adjoint_kernel(const __grid_constant__ Adj
     }
     __syncthreads();
     uint32_t phase = 0;
+    int buf = 0;
 
     for (int64_t tile = blockIdx.x; tile < prm.ntiles; tile += gridDim.x) {
-        const TileDev td = prm.tiles[tile];
-        const ProblemDev<Real>& pu = prm.prob_u[td.problem];
-        const ProblemDev<Real>& pl = prm.prob_l[td.problem];
-        const int64_t nx = pu.nx;
-        const int64_t gj0 = (int64_t)td.local * prm.core - prm.H;
-        const int64_t wabs = pu.base + gj0;
+        AdjTile<Real> at;
+        at.td = prm.tiles[tile];
+        at.pu = &prm.prob_u[at.td.problem];
+        at.pl = &prm.prob_l[at.td.problem];
+        at.gj0 = (int64_t)at.td.local * prm.core - prm.H;
+        at.n0 = prm.n0;
+        at.m0 = prm.m0;
+        at.len = prm.len;
+        const int64_t wabs = at.pu->base + at.gj0;
         if (tid == 0) {
             constexpr uint32_t bytes = W * sizeof(Real);
             bulk_wait_read_all();  // the previous tile's store has read the stage
@@ -98,121 +251,12 @@ __global__ void __launch_bounds__(NT) adjoint_kernel(const __grid_constant__ Adj
             }
             return;
         }
-
-        const int64_t gj = gj0 + (int64_t)tid * P;
-        const Real c2 = pu.c2, kk = pu.k;
-        const bool edge = (gj0 <= 0) || (gj0 + W - 1 >= nx - 1);
-        const bool has_src = pl.js >= 0 && pl.js >= gj0 && pl.js < gj0 + W;
-        const int len = prm.len;
-
-        // ---- u phase: levels n0 .. n0+len-1, Laplacians of every level to shared memory
-        {
-            Real u[P], w[P];
-            smem_to_regs<Real, P>(stage + 0 * W + tid * P, u);
-            smem_to_regs<Real, P>(stage + 1 * W + tid * P, w);
-            const Special sp = special_points<Real, P>(gj, nx, -1);
-            const bool special = edge && is_special(sp, P);
-            int buf = 0;
-            for (int s = 0; s < len; ++s) {
-                Real lft, rgt;
-                exchange<Real, P, NW>(u, lft, rgt, xch, buf, warp, lane);
-                buf ^= 1;
-                Real* lp = laps + s * W + tid * P;
-                const bool step = s + 1 < len;
-                // one pass: the Laplacian of this level (from the step's own neighbour
-                // sum, (uL + uR) - 2u = fma(-2, u, uL + uR) exactly) and the step
-                if constexpr (FORM == kCanonical) {
-                    Real ul = lft;
-#pragma unroll
-                    for (int i = 0; i < P; ++i) {
-                        const Real uc = u[i];
-                        const Real ur = i < P - 1 ? u[i + 1] : rgt;
-                        const Real sum = radd(ul, ur);
-                        lp[i] = rfma(Real(-2), uc, sum);
-                        if (step) {
-                            u[i] = rfma(c2, sum, rfma(kk, uc, -w[i]));
-                            w[i] = uc;
-                        }
-                        ul = uc;
-                    }
-                } else {
-                    Real d_prev = rsub(u[0], lft);
-#pragma unroll
-                    for (int i = 0; i < P; ++i) {
-                        const Real ur = i < P - 1 ? u[i + 1] : rgt;
-                        const Real d = rsub(ur, u[i]);
-                        const Real lap = rsub(d, d_prev);
-                        d_prev = d;
-                        lp[i] = lap;
-                        if (step) {
-                            const Real v = rfma(c2, lap, w[i]);
-                            w[i] = v;
-                            u[i] = radd(u[i], v);
-                        }
-                    }
-                }
-                if (step && special) {
-                    const int64_t n = prm.n0 + s;
-                    const Real fa_old = pu.fA ? pu.fA[n] : Real(0), fa_new = pu.fA ? pu.fA[n + 1] : Real(0);
-                    const Real fb_old = pu.fB ? pu.fB[n] : Real(0), fb_new = pu.fB ? pu.fB[n + 1] : Real(0);
-                    patch_special<Real, FORM, P>(u, w, sp, Real(0), Real(0), fa_old, fa_new, fb_old, fb_new);
-                }
-            }
-        }
-        __syncthreads();
-
-        // ---- lambda phase: levels m0 .. m0+len-1 pair with u levels n0+len-1 .. n0
-        Real racc = Real(0);
-        {
-            Real l[P], lw[P];
-            smem_to_regs<Real, P>(stage + 2 * W + tid * P, l);
-            smem_to_regs<Real, P>(stage + 3 * W + tid * P, lw);
-            const Special sp = special_points<Real, P>(gj, nx, has_src ? pl.js : -1);
-            const bool special = (edge || has_src) && is_special(sp, P);
-            // core points that are interior grid points: [lo, hi) in local thread indices
-            const int64_t core_lo = gj0 + prm.H, core_hi = core_lo + prm.core;
-            const int64_t jlo = core_lo > 1 ? core_lo : 1;
-            const int64_t jhi = core_hi < nx - 1 ? core_hi : nx - 1;
-            int buf = 0;
-            for (int s = 0; s < len; ++s) {
-                Real lft, rgt;
-                exchange<Real, P, NW>(l, lft, rgt, xch, buf, warp, lane);
-                buf ^= 1;
-                const int64_t m = prm.m0 + s;
-                if (td.probe_end > td.probe_begin)
-                    record_probes<Real, P>(l, lft, rgt, wabs, tid * P, 0, P, td.probe_begin, td.probe_end, prm.probes, m);
-                const Real* lp = laps + (len - 1 - s) * W + tid * P;
-#pragma unroll
-                for (int i = 0; i < P; ++i) {
-                    const int64_t j = gj + i;
-                    if (j >= jlo && j < jhi) racc = rfma(l[i], lp[i], racc);
-                }
-                if (special) {
-                    const Real sval = sp.rs >= 0 ? pl.src[(m + 1) * pl.src_stride] : Real(0);
-                    // the increment form adds the source to v before u' = u + v: keep u
-                    const Real uold = (FORM == kIncrement && sp.rs >= 0) ? select_reg<Real, P>(l, sp.rs) : Real(0);
-                    leap_step<Real, FORM, P>(l, lw, lft, rgt, c2, kk);
-                    patch_special<Real, FORM, P>(l, lw, sp, uold, sval, Real(0), Real(0), Real(0), Real(0));
-                } else {
-                    leap_step<Real, FORM, P>(l, lw, lft, rgt, c2, kk);
-                }
-            }
-            __syncthreads();
-            regs_to_smem<Real, P>(stage + 2 * W + tid * P, l);
-            regs_to_smem<Real, P>(stage + 3 * W + tid * P, lw);
-        }
+        const Real racc = adj_tile<Real, FORM, P, NT, SA, 0>(prm, at, stage, laps, xch, buf);
         fence_proxy_async_smem();
-        double acc = (double)racc;
-        // block reduction of acc in a fixed order
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        if (lane == 0) red[warp] = acc;
-        __syncthreads();
+        const double t = block_sum<NT, 0>((double)racc, red);
         if (tid == 0) {
-            double t = 0.0;
-            for (int q = 0; q < NW; ++q) t += red[q];
             prm.partial[tile] = t;
-            const int64_t dst = pu.base + (int64_t)td.local * prm.core;
+            const int64_t dst = at.pu->base + (int64_t)at.td.local * prm.core;
             const uint32_t bytes = (uint32_t)prm.core * sizeof(Real);
             bulk_store(prm.l0_out + dst, stage + 2 * W + prm.H, bytes);
             bulk_store(prm.l1_out + dst, stage + 3 * W + prm.H, bytes);
@@ -220,6 +264,201 @@ __global__ void __launch_bounds__(NT) adjoint_kernel(const __grid_constant__ Adj
         }
     }
     if (tid == 0) bulk_wait_all();
+}
+
+// ---- persistent, warp-specialised adjoint sweep --------------------------------
+// All spans of the adjoint sweep in one launch when the forward state at every
+// span start is kept.  Tickets run over (processing index kp, tile), span
+// K = nspans - 1 - kp (last span first); ticket (kp, i) starts once tiles i-1,
+// i, i+1 have published kp - 1 (their adjoint cores are its halo, and they no
+// longer read the buffer it writes).  A producer warp takes the tickets, loads
+// the four windows of a tile with TMA into one of two stages, stores the
+// adjoint core and publishes; the compute threads run adj_tile with a named
+// barrier among themselves (barrier 1) and write the tile's partial sum.
+
+struct AdjStage {
+    long long ticket;  // -1: no more work
+    int kp;            // processing index (span K = nspans - 1 - kp)
+    int tile;
+    int64_t gj0, n0, m0;
+    int len;
+    int pad_;
+};
+
+template <typename Real, int W>
+__device__ void adj_producer(const AdjParams<Real>& prm, Real* stage, uint64_t* full_bar, uint64_t* empty_bar,
+                             AdjStage* info)
+{
+    const unsigned long long total = (unsigned long long)prm.nspans * (unsigned long long)prm.ntiles;
+    auto grab = [&]() -> long long {
+        if (*(volatile int*)&prm.err->code != 0) return -1;
+        const unsigned long long t = atomicAdd(prm.ticket, 1ull);
+        return t < total ? (long long)t : -1;
+    };
+    auto ready = [&](long long t) -> bool {
+        const int kp = (int)(t / prm.ntiles);
+        if (kp == 0) return true;
+        const int tile = (int)(t % prm.ntiles);
+        const TileDev td = prm.tiles[tile];
+        const int64_t nt = prm.prob_l[td.problem].ntiles;
+        if (ld_acquire(prm.done + tile) < kp) return false;
+        if (td.local > 0 && ld_acquire(prm.done + tile - 1) < kp) return false;
+        if (td.local + 1 < nt && ld_acquire(prm.done + tile + 1) < kp) return false;
+        return true;
+    };
+    auto wait_ready = [&](long long t) -> bool {
+        if (ready(t)) return true;
+        const long long t0 = global_ns();
+        unsigned ns = 32;
+        for (;;) {
+            __nanosleep(ns);
+            if (ns < 1024) ns <<= 1;
+            if (ready(t)) return true;
+            if (*(volatile int*)&prm.err->code != 0) return false;
+            if (global_ns() - t0 > prm.wait_ns) {
+                latch_error(prm.err, kDevTimeoutFlag, (int)(t % prm.ntiles), (int)(t / prm.ntiles), 1);
+                return false;
+            }
+        }
+    };
+    uint32_t fpar = 0u, epar = 0u, armed = 0u;
+    constexpr uint32_t bytes = W * sizeof(Real);
+    auto arm = [&](int y, long long t) {
+        AdjStage& si = info[y];
+        si.ticket = t;
+        if (t >= 0) {
+            const int kp = (int)(t / prm.ntiles);
+            const int tile = (int)(t % prm.ntiles);
+            const int64_t K = (int64_t)prm.nspans - 1 - kp;
+            const TileDev td = prm.tiles[tile];
+            const int64_t gj0 = (int64_t)td.local * prm.core - prm.H;
+            const int64_t wabs = prm.prob_u[td.problem].base + gj0;
+            const int64_t n0 = K * prm.SA;
+            const int len = (int)((prm.T - n0 < prm.SA) ? (prm.T - n0) : prm.SA);
+            si.kp = kp;
+            si.tile = tile;
+            si.gj0 = gj0;
+            si.n0 = n0;
+            si.len = len;
+            si.m0 = prm.T - (n0 + len - 1);
+            Real* st = stage + y * 4 * W;
+            fence_proxy_async_global();
+            mbar_arrive_expect_tx(&full_bar[y], 4 * bytes);
+            bulk_load(st + 0 * W, prm.uck0 + K * prm.ck_stride + wabs, bytes, &full_bar[y]);
+            bulk_load(st + 1 * W, prm.uck1 + K * prm.ck_stride + wabs, bytes, &full_bar[y]);
+            bulk_load(st + 2 * W, prm.lq0[kp & 1] + wabs, bytes, &full_bar[y]);
+            bulk_load(st + 3 * W, prm.lq1[kp & 1] + wabs, bytes, &full_bar[y]);
+        } else {
+            mbar_arrive(&full_bar[y]);
+        }
+        fpar ^= 1u << y;
+        armed |= 1u << y;
+    };
+
+    int y = 0;
+    long long t = grab();
+    if (t >= 0 && !wait_ready(t)) t = -1;
+    arm(0, t);
+    while (t >= 0) {
+        const long long tn = grab();
+        bool next_armed = false;
+        if (tn < 0 || ready(tn)) {
+            arm(y ^ 1, tn);
+            next_armed = true;
+        }
+        if (!mbar_wait_backoff(&empty_bar[y], (epar >> y) & 1u, prm.wait_ns, &prm.err->code)) {
+            latch_error(prm.err, kDevTimeoutLoad, (int)(t % prm.ntiles), (int)(t / prm.ntiles), 1);
+            if (!next_armed) arm(y ^ 1, -1);
+            break;
+        }
+        epar ^= 1u << y;
+        {
+            const AdjStage& si = info[y];
+            const TileDev td = prm.tiles[si.tile];
+            const int64_t dst = prm.prob_u[td.problem].base + (int64_t)td.local * prm.core;
+            const uint32_t cbytes = (uint32_t)prm.core * sizeof(Real);
+            Real* st = stage + y * 4 * W;
+            const int out = (si.kp + 1) & 1;
+            bulk_store(prm.lq0[out] + dst, st + 2 * W + prm.H, cbytes);
+            bulk_store(prm.lq1[out] + dst, st + 3 * W + prm.H, cbytes);
+            bulk_commit();
+            bulk_wait_all();
+            fence_proxy_async_global();
+            __threadfence();
+            st_release(prm.done + si.tile, si.kp + 1);
+        }
+        if (!next_armed) {
+            if (wait_ready(tn)) {
+                arm(y ^ 1, tn);
+            } else {
+                arm(y ^ 1, -1);
+                break;
+            }
+        }
+        t = tn;
+        y ^= 1;
+    }
+    bulk_wait_all();
+    for (int st = 0; st < 2; ++st)
+        if ((armed >> st) & 1u) mbar_wait_bounded(&full_bar[st], ((fpar >> st) & 1u) ^ 1u, prm.wait_ns, nullptr);
+}
+
+template <typename Real, int FORM, int P, int NT, int SA>
+__global__ void __launch_bounds__(NT + 32) adjoint_kernel_ws(const __grid_constant__ AdjParams<Real> prm)
+{
+    constexpr int W = NT * P;
+    constexpr int NW = NT / 32;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Real* stage = reinterpret_cast<Real*>(smem_raw);  // [2 stages][4][W]
+    Real* laps = stage + 8 * W;                       // [SA][W]
+    Real* xch = laps + SA * W;                        // [2][NW][2]
+    __shared__ __align__(8) uint64_t full_bar[2];
+    __shared__ __align__(8) uint64_t empty_bar[2];
+    __shared__ AdjStage s_info[2];
+    __shared__ double red[NW];
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    if (tid == NT) {
+        mbar_init(&full_bar[0], 1);
+        mbar_init(&full_bar[1], 1);
+        mbar_init(&empty_bar[0], NW);
+        mbar_init(&empty_bar[1], NW);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async_smem();
+    }
+    __syncthreads();  // the last CTA-wide barrier: from here on only barrier 1 (compute threads)
+    if (warp == NW) {
+        if (lane == 0) adj_producer<Real, W>(prm, stage, full_bar, empty_bar, s_info);
+        return;
+    }
+    uint32_t fpar = 0u;
+    int y = 0, buf = 0;
+    for (;;) {
+        const bool ok = mbar_wait_bounded(&full_bar[y], (fpar >> y) & 1u, prm.wait_ns, &prm.err->code);
+        fpar ^= 1u << y;
+        if (!ok) latch_error(prm.err, kDevTimeoutLoad, -1, -1, 1);
+        if (block_sync_or<NT>(!ok)) break;  // one decision for all compute threads
+        const AdjStage& si = s_info[y];
+        if (si.ticket < 0) break;
+        AdjTile<Real> at;
+        at.td = prm.tiles[si.tile];
+        at.pu = &prm.prob_u[at.td.problem];
+        at.pl = &prm.prob_l[at.td.problem];
+        at.gj0 = si.gj0;
+        at.n0 = si.n0;
+        at.m0 = si.m0;
+        at.len = si.len;
+        Real* st = stage + y * 4 * W;
+        const Real racc = adj_tile<Real, FORM, P, NT, SA, NT>(prm, at, st, laps, xch, buf);
+        const double t = block_sum<NT, NT>((double)racc, red);
+        if (tid == 0) prm.partial[(int64_t)(prm.nspans - 1 - si.kp) * prm.ntiles + si.tile] = t;
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty_bar[y]);
+        y ^= 1;
+    }
 }
 
 template <typename Real>
@@ -330,6 +569,76 @@ cudaError_t adj_launch(int v, const void* params, int grid, cudaStream_t s)
     const AEntry& e = atable(&n)[v];
     void* args[] = {const_cast<void*>(params)};
     return cudaLaunchKernel(e.fn, dim3(grid), dim3(e.info.NT), args, e.smem, s);
+}
+
+// ---- persistent adjoint kernels (one per dtype / form) -----------------------
+
+namespace {
+
+struct WsEntry {
+    int dtype, form, W, SA;
+    const void* fn;
+    size_t smem;
+};
+
+template <typename Real, int FORM, int P, int NT, int SA>
+WsEntry make_ws()
+{
+    constexpr int W = NT * P;
+    return WsEntry{sizeof(Real) == 8 ? kF64 : kF32, FORM, W, SA,
+                   reinterpret_cast<const void*>(&adjoint_kernel_ws<Real, FORM, P, NT, SA>),
+                   sizeof(Real) * ((8 + SA) * W + 4 * (NT / 32))};
+}
+
+const WsEntry* ws_find(int dtype, int form)
+{
+    static const WsEntry entries[] = {
+        make_ws<double, kCanonical, 4, 128, 8>(),
+        make_ws<double, kIncrement, 4, 128, 8>(),
+        make_ws<float, kIncrement, 8, 128, 16>(),
+        make_ws<float, kCanonical, 8, 128, 16>(),
+    };
+    for (const WsEntry& e : entries)
+        if (e.dtype == dtype && e.form == form) return &e;
+    return nullptr;
+}
+
+}  // namespace
+
+int adj_ws_span(int dtype, int form)
+{
+    const WsEntry* e = ws_find(dtype, form);
+    return e ? e->SA : 0;
+}
+
+int adj_ws_window(int dtype, int form)
+{
+    const WsEntry* e = ws_find(dtype, form);
+    return e ? e->W : 0;
+}
+
+cudaError_t adj_ws_prepare(int dtype, int form)
+{
+    const WsEntry* e = ws_find(dtype, form);
+    if (!e) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(e->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem);
+}
+
+cudaError_t adj_ws_occupancy(int dtype, int form, int* blocks_per_sm)
+{
+    const WsEntry* e = ws_find(dtype, form);
+    if (!e) return cudaErrorInvalidValue;
+    cudaError_t st = adj_ws_prepare(dtype, form);
+    if (st != cudaSuccess) return st;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, e->fn, 128 + 32, e->smem);
+}
+
+cudaError_t adj_ws_launch(int dtype, int form, const void* params, int grid, cudaStream_t s)
+{
+    const WsEntry* e = ws_find(dtype, form);
+    if (!e) return cudaErrorInvalidValue;
+    void* args[] = {const_cast<void*>(params)};
+    return cudaLaunchKernel(e->fn, dim3(grid), dim3(128 + 32), args, e->smem, s);
 }
 
 cudaError_t adj_init_launch(int dtype, int form, void* l0, void* l1, const void* prob_l, int nprob, const void* wbar,

@@ -86,6 +86,7 @@ struct Engine {
     int variant = 0;
     int mode = RSWR_MODE_PERSISTENT;
     double wait_s = 5.0;
+    int64_t ck_spacing = 0;  // adjoint checkpoint spacing in spans (0: automatic)
     int S = 1, H = 4, W = 0, core = 0, P = 0, NT = 0;
     int inject_tile = -1, inject_span = -1;
     bool is_plan = true;
@@ -854,40 +855,62 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     const int vf = e->variant;
     const VariantInfo fi = span_variant_info(vf);
     const int core_f = fi.W - 2 * H;
-    const int core_a = ai.W - 2 * H;
-    if (core_f < H || core_a < H) return fail(RSWR_EINVAL, "adjoint tiling: window too small");
     const int64_t pad = H + 8;
+    const int64_t nspans = (T + SA - 1) / SA;
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
 
     // layout shared by the forward tiling (core_f) and the adjoint tiling (core_a)
     std::vector<int64_t> base(np), t0f(np), tcf(np), t0a(np), tca(np);
-    int64_t at = 0, ntf = 0, nta = 0;
-    for (int p = 0; p < np; ++p) {
-        const int64_t nx = e->probs[p].nx;
-        tcf[p] = (nx + core_f - 1) / core_f;
-        tca[p] = (nx + core_a - 1) / core_a;
-        t0f[p] = ntf;
-        t0a[p] = nta;
-        ntf += tcf[p];
-        nta += tca[p];
-        base[p] = at + pad;
-        int64_t len = pad + std::max(tcf[p] * core_f, tca[p] * core_a) + pad;
-        at += (len + kAlign - 1) / kAlign * kAlign;
-    }
-    const int64_t slen = at;
-    const int64_t nspans = (T + SA - 1) / SA;
-    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
-    const size_t arr = up(es * slen);
+    int64_t ntf = 0, nta = 0, slen = 0;
+    size_t arr = 0;
+    int core_a = 0;
+    auto make_layout = [&](int ca) {
+        core_a = ca;
+        int64_t at = 0;
+        ntf = nta = 0;
+        for (int p = 0; p < np; ++p) {
+            const int64_t nx = e->probs[p].nx;
+            tcf[p] = (nx + core_f - 1) / core_f;
+            tca[p] = (nx + core_a - 1) / core_a;
+            t0f[p] = ntf;
+            t0a[p] = nta;
+            ntf += tcf[p];
+            nta += tca[p];
+            base[p] = at + pad;
+            int64_t len = pad + std::max(tcf[p] * core_f, tca[p] * core_a) + pad;
+            at += (len + kAlign - 1) / kAlign * kAlign;
+        }
+        slen = at;
+        arr = up(es * slen);
+    };
     // Checkpoint spacing: every span boundary when all of them fit in half of the
     // free device memory (no recompute sweep), else sqrt(#spans) of them.
-    int64_t C = std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)std::max<int64_t>(nspans, 1))));
-    {
+    auto spacing = [&]() -> int64_t {
+        if (e->ck_spacing > 0) return std::min<int64_t>(e->ck_spacing, std::max<int64_t>(nspans, 1));
+        int64_t c = std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)std::max<int64_t>(nspans, 1))));
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
             const size_t avail = free_b + e->adj_mem_cap;
-            if ((size_t)(nspans + 6) * 2 * arr < avail / 2) C = 1;
+            if ((size_t)(nspans + 6) * 2 * arr < avail / 2) c = 1;
         } else {
             cudaGetLastError();
         }
+        return c;
+    };
+    // With every span state kept the whole adjoint sweep is one persistent launch
+    // (its own window); otherwise one launch of the per-span kernel per span.
+    const int w_ws = adj_ws_window(e->dtype, e->form);
+    bool use_ws = w_ws > 0 && adj_ws_span(e->dtype, e->form) >= SA && w_ws - 2 * H >= H;
+    if (core_f < H || ai.W - 2 * H < H) return fail(RSWR_EINVAL, "adjoint tiling: window too small");
+    int64_t C;
+    if (use_ws) {
+        make_layout(w_ws - 2 * H);
+        C = spacing();
+        if (C != 1) use_ws = false;
+    }
+    if (!use_ws) {
+        make_layout(ai.W - 2 * H);
+        C = spacing();
     }
     const int64_t nck = std::max<int64_t>(1, (nspans + C - 1) / C);
     const int64_t nstates = nck + C + 4;  // checkpoints | segment | forward work pair | adjoint pair
@@ -899,7 +922,8 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     const size_t b_prob = up(sizeof(ProblemDev<Real>) * 2 * np);
     const size_t b_probes = up(sizeof(ProbeDev<Real>) * np);
     const size_t b_red = up(sizeof(int64_t) * 2 * np + sizeof(double) * np);
-    const size_t need = b_states + b_partial + b_tiles + b_prob + b_probes + b_red;
+    const size_t b_done = up(sizeof(int) * std::max<int64_t>(ntf, nta));
+    const size_t need = b_states + b_partial + b_tiles + b_prob + b_probes + b_red + b_done;
     if (need > e->adj_mem_cap) {
         RSWR_CUDA(cudaStreamSynchronize(s));
         cudaFree(e->adj_mem);
@@ -928,6 +952,8 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     int64_t* d_t0 = reinterpret_cast<int64_t*>(q);
     int64_t* d_tc = d_t0 + np;
     double* d_scale = reinterpret_cast<double*>(d_tc + np);
+    q += b_red;
+    int* d_done = reinterpret_cast<int*>(q);
     const int64_t CK0 = 0, SG0 = nck, WK0 = nck + C, LM0 = nck + C + 2;
 
     // host tables
@@ -1038,11 +1064,30 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     RSWR_CUDA(cudaMemsetAsync(state0(CK0), 0, 2 * arr, s));
     RSWR_CUDA(set_boundary_launch(e->dtype, e->form, state0(CK0), state1(CK0), d_pu, np, s));
     const int64_t last_ck_span = (nck - 1) * C;
-    for (int64_t k = 0; k < last_ck_span; ++k) {
-        const int64_t si = (k % C == 0) ? CK0 + k / C : WK0 + (k & 1);
-        const int64_t di = ((k + 1) % C == 0) ? CK0 + (k + 1) / C : WK0 + ((k + 1) & 1);
-        rswr_status st = forward_span(k, state0(si), state1(si), state0(di), state1(di));
-        if (st != RSWR_OK) return st;
+    if (C == 1 && last_ck_span > 0) {
+        // every span state is kept: the whole sweep is one persistent launch in
+        // which span k reads state k and writes state k + 1 (neighbour flags as in
+        // rswr_run; the states are distinct arrays, so only read-after-write waits)
+        SpanParams<Real> cp = fp;
+        cp.span = -1;
+        cp.nspans = (int32_t)last_ck_span;
+        cp.ck_stride = (int64_t)(2 * arr / es);
+        cp.q0[0] = state0(CK0);
+        cp.q1[0] = state1(CK0);
+        cp.q0[1] = cp.q1[1] = nullptr;
+        cp.ticket = static_cast<unsigned long long*>(e->d_ticket);
+        cp.done = d_done;
+        RSWR_CUDA(cudaMemsetAsync(e->d_ticket, 0, sizeof(unsigned long long), s));
+        RSWR_CUDA(cudaMemsetAsync(d_done, 0, sizeof(int) * ntf, s));
+        const int grid = (int)std::min<int64_t>((int64_t)std::max(bps_f, 1) * e->num_sms, last_ck_span * ntf);
+        RSWR_CUDA(span_launch(vf, &cp, grid, s));
+    } else {
+        for (int64_t k = 0; k < last_ck_span; ++k) {
+            const int64_t si = (k % C == 0) ? CK0 + k / C : WK0 + (k & 1);
+            const int64_t di = ((k + 1) % C == 0) ? CK0 + (k + 1) / C : WK0 + ((k + 1) & 1);
+            rswr_status st = forward_span(k, state0(si), state1(si), state0(di), state1(di));
+            if (st != RSWR_OK) return st;
+        }
     }
 
     // adjoint sweep
@@ -1059,7 +1104,32 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     ap.err = e->d_err;
     ap.wait_ns = (long long)(e->wait_s * 1e9);
     int cur = 0;
-    for (int64_t g = nck - 1; g >= 0; --g) {
+    if (use_ws) {
+        // all spans, last first, in one launch; the forward state at the start of
+        // span K is checkpoint K (C == 1)
+        AdjParams<Real> wp = ap;
+        wp.partial = partial;
+        wp.uck0 = state0(CK0);
+        wp.uck1 = state1(CK0);
+        wp.ck_stride = (int64_t)(2 * arr / es);
+        wp.lq0[0] = state0(LM0);
+        wp.lq1[0] = state1(LM0);
+        wp.lq0[1] = state0(LM0 + 1);
+        wp.lq1[1] = state1(LM0 + 1);
+        wp.T = T;
+        wp.SA = SA;
+        wp.nspans = (int32_t)nspans;
+        wp.ticket = static_cast<unsigned long long*>(e->d_ticket);
+        wp.done = d_done;
+        int bps_w = 0;
+        RSWR_CUDA(adj_ws_occupancy(e->dtype, e->form, &bps_w));
+        if (bps_w < 1) return fail(RSWR_ENOTSUP, "adjoint kernel does not fit on an SM");
+        RSWR_CUDA(cudaMemsetAsync(e->d_ticket, 0, sizeof(unsigned long long), s));
+        RSWR_CUDA(cudaMemsetAsync(d_done, 0, sizeof(int) * nta, s));
+        const int grid = (int)std::min<int64_t>((int64_t)bps_w * e->num_sms, nspans * nta);
+        if (nspans > 0) RSWR_CUDA(adj_ws_launch(e->dtype, e->form, &wp, grid, s));
+    }
+    for (int64_t g = use_ws ? -1 : nck - 1; g >= 0; --g) {
         const int64_t k_lo = g * C, k_hi = std::min<int64_t>((g + 1) * C, nspans);
         auto seg = [&](int64_t i) { return i == 0 ? CK0 + g : SG0 + i; };
         for (int64_t k = k_lo; k + 1 < k_hi; ++k) {
@@ -1489,6 +1559,14 @@ rswr_status rswr_plan_set_wait_limit(rswr_plan_t plan, double seconds)
     return RSWR_OK;
 }
 
+rswr_status rswr_plan_set_checkpoint_spacing(rswr_plan_t plan, int64_t spans)
+{
+    if (!plan) return fail(RSWR_EINVAL, "NULL plan");
+    if (spans < 0) return fail(RSWR_EINVAL, "checkpoint spacing must be >= 0");
+    plan->e->ck_spacing = spans;
+    return RSWR_OK;
+}
+
 rswr_status rswr_plan_inject_missing_flag(rswr_plan_t plan, int32_t tile, int32_t span)
 {
     if (!plan) return fail(RSWR_EINVAL, "NULL plan");
@@ -1644,6 +1722,14 @@ rswr_status rswr_batch_set_wait_limit(rswr_batch_t batch, double seconds)
     if (!batch) return fail(RSWR_EINVAL, "NULL batch");
     if (!(seconds > 0.0) || seconds > 3600.0) return fail(RSWR_EINVAL, "wait limit out of range");
     batch->e->wait_s = seconds;
+    return RSWR_OK;
+}
+
+rswr_status rswr_batch_set_checkpoint_spacing(rswr_batch_t batch, int64_t spans)
+{
+    if (!batch) return fail(RSWR_EINVAL, "NULL batch");
+    if (spans < 0) return fail(RSWR_EINVAL, "checkpoint spacing must be >= 0");
+    batch->e->ck_spacing = spans;
     return RSWR_OK;
 }
 

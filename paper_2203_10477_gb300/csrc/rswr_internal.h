@@ -71,6 +71,9 @@ struct SpanParams {
     int* done;                   // persistent mode: spans completed per tile (zeroed per launch)
     DevError* err;
     long long wait_ns;           // bound of every device-side wait
+    int64_t ck_stride;           // 0: span k reads q[k & 1] and writes q[(k + 1) & 1];
+                                 // > 0: span k reads q[0] + k * ck_stride and writes
+                                 // q[0] + (k + 1) * ck_stride (every span state kept)
 };
 
 template <typename Real>
@@ -116,6 +119,19 @@ struct AdjParams {
     int32_t pad_;
     DevError* err;
     long long wait_ns;
+    // persistent sweep over all spans (every span-start state of the forward
+    // problem kept): span K starts from uck0/uck1 + K * ck_stride; lambda
+    // ping-pongs between lq0/lq1[0] and [1]; the spans run last first
+    const Real* uck0;
+    const Real* uck1;
+    int64_t ck_stride;
+    Real* lq0[2];
+    Real* lq1[2];
+    int64_t T;
+    int32_t SA;
+    int32_t nspans;
+    unsigned long long* ticket;
+    int* done;
 };
 
 // The paper-literal span (paper_kernel.cu): plain (unpadded) state arrays.
@@ -165,6 +181,12 @@ int adj_variant_span(int v);  // largest span the variant's shared-memory store 
 cudaError_t adj_prepare(int v);
 cudaError_t adj_occupancy(int v, int* blocks_per_sm);
 cudaError_t adj_launch(int v, const void* params, int grid, cudaStream_t s);
+// persistent sweep over all spans (AdjParams' persistent fields), warp-specialised
+cudaError_t adj_ws_prepare(int dtype, int form);
+cudaError_t adj_ws_occupancy(int dtype, int form, int* blocks_per_sm);
+cudaError_t adj_ws_launch(int dtype, int form, const void* params, int grid, cudaStream_t s);
+int adj_ws_span(int dtype, int form);    // span the persistent kernel's Laplacian store holds (0: none)
+int adj_ws_window(int dtype, int form);  // points per CTA window of the persistent kernel
 // lambda at level 1 of the reversed-time sweep: wbar[T] at j_r (interior receivers only)
 cudaError_t adj_init_launch(int dtype, int form, void* l0, void* l1, const void* prob_l, int nprob,
                             const void* wbar, int64_t T, cudaStream_t s);

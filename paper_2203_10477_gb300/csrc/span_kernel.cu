@@ -91,6 +91,15 @@ __device__ bool wait_deps(const SpanParams<Real>& prm, long long t)
     }
 }
 
+// State arrays read (span k) and written (span k + 1) by a span; comp 0 / 1
+// selects the first / second component.
+template <typename Real>
+__device__ __forceinline__ Real* span_state(const SpanParams<Real>& prm, int comp, int level_span)
+{
+    Real* const* q = comp ? prm.q1 : prm.q0;
+    return prm.ck_stride ? q[0] + (int64_t)level_span * prm.ck_stride : q[level_span & 1];
+}
+
 template <typename Real, int W>
 __device__ __forceinline__ void issue_load(const SpanParams<Real>& prm, long long t, Real* stage_y, uint64_t* bar)
 {
@@ -101,8 +110,8 @@ __device__ __forceinline__ void issue_load(const SpanParams<Real>& prm, long lon
     constexpr uint32_t bytes = W * sizeof(Real);
     fence_proxy_async_global();
     mbar_arrive_expect_tx(bar, 2 * bytes);
-    bulk_load(stage_y, prm.q0[k & 1] + off, bytes, bar);
-    bulk_load(stage_y + W, prm.q1[k & 1] + off, bytes, bar);
+    bulk_load(stage_y, span_state(prm, 0, k) + off, bytes, bar);
+    bulk_load(stage_y + W, span_state(prm, 1, k) + off, bytes, bar);
 }
 
 // Caller guarantees that the bulk store of ticket t has completed.
@@ -414,9 +423,8 @@ __global__ void __launch_bounds__(NT, MINB) span_kernel(const __grid_constant__ 
         if (tid == 0) {
             const int64_t dst = pr.base + (int64_t)td.local * prm.core;
             const uint32_t bytes = (uint32_t)prm.core * sizeof(Real);
-            const int b = (k + 1) & 1;
-            bulk_store(prm.q0[b] + dst, su + prm.H, bytes);
-            bulk_store(prm.q1[b] + dst, sw + prm.H, bytes);
+            bulk_store(span_state(prm, 0, k + 1) + dst, su + prm.H, bytes);
+            bulk_store(span_state(prm, 1, k + 1) + dst, sw + prm.H, bytes);
             bulk_commit();
             if (pending >= 0) {
                 // the store of the previous tile is complete once at most one group is pending
@@ -556,10 +564,9 @@ __device__ void producer_loop(const SpanParams<Real>& prm, Real* stage, uint64_t
             const StageInfo<Real>& si = info[y];
             const int64_t dst = si.pr.base + (int64_t)si.td.local * prm.core;
             const uint32_t bytes = (uint32_t)prm.core * sizeof(Real);
-            const int b = (si.k + 1) & 1;
             Real* su = stage + y * 2 * W;
-            bulk_store(prm.q0[b] + dst, su + prm.H, bytes);
-            bulk_store(prm.q1[b] + dst, su + W + prm.H, bytes);
+            bulk_store(span_state(prm, 0, si.k + 1) + dst, su + prm.H, bytes);
+            bulk_store(span_state(prm, 1, si.k + 1) + dst, su + W + prm.H, bytes);
             bulk_commit();
             bulk_wait_all();
             publish(prm, t);

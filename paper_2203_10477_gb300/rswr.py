@@ -73,6 +73,7 @@ SIGNATURES = {
     "rswr_plan_set_variant": (_st, [_vp, _i32]),
     "rswr_plan_set_mode": (_st, [_vp, _i32]),
     "rswr_plan_set_wait_limit": (_st, [_vp, _dbl]),
+    "rswr_plan_set_checkpoint_spacing": (_st, [_vp, _i64]),
     "rswr_plan_inject_missing_flag": (_st, [_vp, _i32, _i32]),
     "rswr_plan_autotune": (_st, [_vp, _i64, ctypes.POINTER(_i32), _vp]),
     "rswr_plan_set_kernel_events": (_st, [_vp, _vp, _vp]),
@@ -93,6 +94,7 @@ SIGNATURES = {
     "rswr_batch_set_mode": (_st, [_vp, _i32]),
     "rswr_batch_set_variant": (_st, [_vp, _i32]),
     "rswr_batch_set_wait_limit": (_st, [_vp, _dbl]),
+    "rswr_batch_set_checkpoint_spacing": (_st, [_vp, _i64]),
     "rswr_batch_check": (_st, [_vp, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "rswr_batch_run": (_st, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "rswr_batch_adjoint": (_st, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]),
@@ -225,6 +227,10 @@ class Plan:
 
     def set_wait_limit(self, seconds: float):
         check(lib().rswr_plan_set_wait_limit(self.h, seconds))
+
+    def set_checkpoint_spacing(self, spans: int):
+        """Adjoint checkpoint every `spans` spans (0: automatic)."""
+        check(lib().rswr_plan_set_checkpoint_spacing(self.h, spans))
 
     def set_graph(self, enable: bool):
         check(lib().rswr_plan_set_graph(self.h, int(enable)))
@@ -377,6 +383,9 @@ class Batch:
 
     def set_wait_limit(self, seconds: float):
         check(lib().rswr_batch_set_wait_limit(self.h, seconds))
+
+    def set_checkpoint_spacing(self, spans: int):
+        check(lib().rswr_batch_set_checkpoint_spacing(self.h, spans))
 
     def set_graph(self, enable: bool):
         check(lib().rswr_batch_set_graph(self.h, int(enable)))

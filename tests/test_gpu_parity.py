@@ -356,20 +356,24 @@ def test_autograd_function_matches_oracle(R, oracle_mod):
 # adjoint: gradient w.r.t. the wave speed (checkpointed forward, in-SMEM recompute)
 # ----------------------------------------------------------------------------
 
+# spacing 0: automatic (every span state kept, one persistent adjoint launch);
+# > 0: a checkpoint every `spacing` spans, segments recomputed, one launch per span
+@pytest.mark.parametrize("spacing", [0, 7])
 @pytest.mark.parametrize("nx,N,ov,T,jr", [
-    (301, 3, 16, 420, 120),      # 53 spans of 8 steps, 8 segments
-    (2001, 4, 64, 2003, 777),    # ragged last span, 16 segments
+    (301, 3, 16, 420, 120),      # 53 spans of 8 steps (8 segments when spaced)
+    (2001, 4, 64, 2003, 777),    # ragged last span
     (4099, 2, 10, 333, 2000),    # S = 5
     (301, 3, 16, 420, 0),        # receiver on the Dirichlet node: dL/da = 0
     (301, 3, 16, 50, 250),       # receiver out of reach: everything 0
 ])
-def test_adjoint_grad_a_fp64(R, oracle_mod, nx, N, ov, T, jr):
+def test_adjoint_grad_a_fp64(R, oracle_mod, nx, N, ov, T, jr, spacing):
     a = 1.3
     dt = 0.9 / (nx - 1) / a
     g = inputs.lowpass_noise(T, seed=21)
     z = np.zeros(T + 1)
     w = inputs.rng(5).standard_normal(T + 1)
     plan = R.Plan(0.0, 1.0, a, nx, dt, N, ov, dtype=F64)
+    plan.set_checkpoint_spacing(spacing)
     res = plan.adjoint(g, None, T, jr, w, want_a=True)
     plan.check()
     ref = oracle_mod.adjoint(nx, T, a, dt, g, z, jr, w)
@@ -380,13 +384,15 @@ def test_adjoint_grad_a_fp64(R, oracle_mod, nx, N, ov, T, jr):
         assert da == 0.0
 
 
-def test_adjoint_grad_a_fp32(R, oracle_mod):
+@pytest.mark.parametrize("spacing", [0, 11])
+def test_adjoint_grad_a_fp32(R, oracle_mod, spacing):
     nx, N, ov, T, jr = 3001, 4, 64, 2000, 1200
     a = 1.3
     dt = 0.9 / (nx - 1) / a
     g = inputs.lowpass_noise(T, seed=2)
     w = inputs.rng(6).standard_normal(T + 1)
     plan = R.Plan(0.0, 1.0, a, nx, dt, N, ov, dtype=F32)
+    plan.set_checkpoint_spacing(spacing)
     res = plan.adjoint(g, None, T, jr, w, want_a=True)
     ref = oracle_mod.adjoint(nx, T, a, dt, g, np.zeros(T + 1), jr, w)
     da = res["grad_a"].item()
@@ -395,7 +401,8 @@ def test_adjoint_grad_a_fp32(R, oracle_mod):
     assert np.linalg.norm(got - ref["dg"]) <= 1e-4 * np.linalg.norm(ref["dg"])
 
 
-def test_batch_adjoint_with_grad_a(R, oracle_mod):
+@pytest.mark.parametrize("spacing", [0, 5])
+def test_batch_adjoint_with_grad_a(R, oracle_mod, spacing):
     r = inputs.rng(17)
     T = 400
     probs, jrs = [], []
@@ -407,6 +414,7 @@ def test_batch_adjoint_with_grad_a(R, oracle_mod):
                                     np.zeros(T + 1)))
         jrs.append(int(r.integers(1, min(nx - 1, T))))
     b = R.Batch(probs, dtype=F64)
+    b.set_checkpoint_spacing(spacing)
     fA = np.concatenate([p.fA for p in probs])
     w = inputs.rng(18).standard_normal((len(probs), T + 1))
     res = b.adjoint(fA, None, T, jrs, w, want_a=True)
