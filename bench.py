@@ -110,7 +110,22 @@ class ClockSampler:
         self.proc = None
         self.path = None
 
+    def other_processes(self):
+        """Compute processes on this GPU other than this one (a shared GPU skews timing)."""
+        try:
+            out = subprocess.run(["nvidia-smi", "-i", self.gpu_id, "--query-compute-apps=pid,used_memory",
+                                  "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10).stdout
+        except Exception:
+            return None
+        pids = []
+        for line in out.splitlines():
+            parts = [q.strip() for q in line.split(",")]
+            if parts and parts[0].isdigit() and int(parts[0]) != os.getpid():
+                pids.append(int(parts[0]))
+        return pids
+
     def start(self):
+        self.others = set(self.other_processes() or [])
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
@@ -124,6 +139,7 @@ class ClockSampler:
     def stop(self):
         if self.proc is None:
             return None
+        self.others |= set(self.other_processes() or [])
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -151,7 +167,8 @@ class ClockSampler:
                     reasons.add(name)
         loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
         return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": sorted(reasons), "samples": len(rows)}
+                "reasons": sorted(reasons), "samples": len(rows),
+                "other_gpu_processes": sorted(self.others)}
 
 
 # ----------------------------------------------------------------------------
