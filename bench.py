@@ -330,10 +330,11 @@ def e2e_run(torch, plan, p, steps):
 def profile_case(which: str, variant=None, span=None, full=False) -> None:
     """The bench workload (full = True) or its small version for detailed
     captures: nx = 2^22, 256 subdomains (the bench's subdomain length of 16384
-    points, so the same share of tiles carries interface probes) and 320 steps
-    (10 spans); four state arrays of 32 MiB (FP64) / 16 MiB (FP32), so DRAM
-    counters still see traffic beyond L2.  Runs the workload twice (the first
-    run warms up)."""
+    points, so the same share of tiles carries interface probes) and 1280 steps
+    (40 spans of 32, so the fill and drain of the span pipeline are a small
+    part); four state arrays of 32 MiB (FP64) / 16 MiB (FP32), so DRAM counters
+    still see traffic beyond L2.  Runs the workload twice (the first run warms
+    up).  adj64 / adj32: the c4 gradient workload (dL/dfA and dL/da)."""
     import dataclasses
 
     import torch
@@ -358,7 +359,7 @@ def profile_case(which: str, variant=None, span=None, full=False) -> None:
     if full:
         p = inputs.c2()
     else:
-        p = inputs.c2(T=320, nx=1 << 22)
+        p = inputs.c2(T=1280, nx=1 << 22)
         p = dataclasses.replace(p, n_sub=p.nx // 16384)
     plan = rswr.Plan.from_problem(p, dtype=rswr.F64 if which == "f64" else rswr.F32)
     if span is not None:
@@ -538,7 +539,7 @@ def main():
     ap.add_argument("--no-mono", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched / adjoint / large-grid measurements")
     ap.add_argument("--profile-case", choices=["f64", "f32", "adj64", "adj32"], default=None,
-                    help="run the small profiling case (nx=2^22, 320 steps) twice and exit (for ncu)")
+                    help="run the small profiling case (nx=2^22, 1280 steps) twice and exit (for ncu)")
     ap.add_argument("--variant", type=int, default=None, help="kernel variant of the profiling case")
     ap.add_argument("--span", type=int, default=None, help="steps per span of the profiling case")
     ap.add_argument("--full", action="store_true", help="profiling case at the bench's full size")

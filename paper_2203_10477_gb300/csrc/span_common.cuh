@@ -425,6 +425,69 @@ __device__ __forceinline__ void warp_neighbours(const Real (&u)[P], Real& lft, R
     if (lane == 31) rgt = u[P - 2];
 }
 
+// `steps` leapfrog steps of a warp window (neighbours by shuffles, mirror
+// ghosts at the window's ends) in the order: the thread's two end points, the
+// shuffles of their new values for the next step, then the interior points,
+// so that the shuffle latency hides behind the interior updates.  Every update
+// is the same expression on the same operands as leap_step(), so the bits are
+// identical.
+template <typename Real, int FORM, int P>
+__device__ __forceinline__ void warp_steps_edges_first(Real (&u)[P], Real (&w)[P], Real c2, Real k, int steps,
+                                                       int lane)
+{
+    static_assert(P >= 3, "edges-first order needs interior points");
+    Real lft, rgt;
+    warp_neighbours<Real, P>(u, lft, rgt, lane);
+    for (int s = 0; s < steps; ++s) {
+        Real n0, nl, v0, vl;  // new first / last point and their second components
+        Real d0 = Real(0);
+        if constexpr (FORM == kIncrement) {
+            d0 = rsub(u[1], u[0]);
+            const Real dm = rsub(u[P - 1], u[P - 2]);
+            v0 = rfma(c2, rsub(d0, rsub(u[0], lft)), w[0]);
+            vl = rfma(c2, rsub(rsub(rgt, u[P - 1]), dm), w[P - 1]);
+            n0 = radd(u[0], v0);
+            nl = radd(u[P - 1], vl);
+        } else {
+            n0 = rfma(c2, radd(lft, u[1]), rfma(k, u[0], -w[0]));
+            v0 = u[0];
+            nl = rfma(c2, radd(u[P - 2], rgt), rfma(k, u[P - 1], -w[P - 1]));
+            vl = u[P - 1];
+        }
+        Real nlft = __shfl_up_sync(kFull, nl, 1);
+        Real nrgt = __shfl_down_sync(kFull, n0, 1);
+        if constexpr (FORM == kIncrement) {
+            Real dprev = d0;
+#pragma unroll
+            for (int i = 1; i < P - 1; ++i) {
+                const Real d = rsub(u[i + 1], u[i]);
+                const Real v = rfma(c2, rsub(d, dprev), w[i]);
+                dprev = d;
+                w[i] = v;
+                u[i] = radd(u[i], v);
+            }
+        } else {
+            Real ul = u[0];
+#pragma unroll
+            for (int i = 1; i < P - 1; ++i) {
+                const Real uc = u[i];
+                const Real un = rfma(c2, radd(ul, u[i + 1]), rfma(k, uc, -w[i]));
+                w[i] = uc;
+                u[i] = un;
+                ul = uc;
+            }
+        }
+        u[0] = n0;
+        w[0] = v0;
+        u[P - 1] = nl;
+        w[P - 1] = vl;
+        if (lane == 0) nlft = u[1];
+        if (lane == 31) nrgt = u[P - 2];
+        lft = nlft;
+        rgt = nrgt;
+    }
+}
+
 // Write the registers a thread owns, [own_lo, own_hi), back to the shared window.
 template <typename Real, int P, int KH>
 __device__ __forceinline__ void owned_to_smem(Real* s, const Real (&r)[P], int own_lo, int own_hi)

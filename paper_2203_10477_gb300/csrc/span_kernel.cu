@@ -114,6 +114,22 @@ __device__ __forceinline__ void issue_load(const SpanParams<Real>& prm, long lon
     bulk_load(stage_y + W, span_state(prm, 1, k) + off, bytes, bar);
 }
 
+// The same copies for the warp-specialised producer: the bytes are expected
+// without an arrival (the producer arrives once the stage's record is written).
+template <typename Real, int W>
+__device__ __forceinline__ void issue_load_tx(const SpanParams<Real>& prm, long long t, Real* stage_y, uint64_t* bar)
+{
+    const int k = (int)(t / prm.ntiles);
+    const int tile = (int)(t % prm.ntiles);
+    const TileDev td = prm.tiles[tile];
+    const int64_t off = prm.problems[td.problem].base + (int64_t)td.local * prm.core - prm.H;
+    constexpr uint32_t bytes = W * sizeof(Real);
+    fence_proxy_async_global();
+    mbar_expect_tx(bar, 2 * bytes);
+    bulk_load(stage_y, span_state(prm, 0, k) + off, bytes, bar);
+    bulk_load(stage_y + W, span_state(prm, 1, k) + off, bytes, bar);
+}
+
 // Caller guarantees that the bulk store of ticket t has completed.
 template <typename Real>
 __device__ __forceinline__ void publish(const SpanParams<Real>& prm, long long t)
@@ -210,6 +226,11 @@ __device__ __forceinline__ void predict_tile(const SpanParams<Real>& prm, const 
         }
         Special sp{-1, -1, -1, 0, P - 1};
         if constexpr (SP) sp = special_points();
+        if constexpr (KH > 0 && !PR && !SP) {
+            // plain interior tile of a warp window: the bare stencil, edges first
+            warp_steps_edges_first<Real, FORM, P>(u, w, c2, kk, s_end - s_begin, lane);
+            return;
+        }
         for (int s = s_begin; s < s_end; ++s) {
             Real lft, rgt;
             if constexpr (KH > 0) {
@@ -510,6 +531,50 @@ __device__ void producer_loop(const SpanParams<Real>& prm, Real* stage, uint64_t
     uint32_t epar = 0u;   // bit y: parity of the next phase of empty_bar[y]
     uint32_t armed = 0u;  // bit y: full_bar[y] has been armed at least once
 
+    // tile count of the problem of the last ticket looked at (consecutive
+    // tiles mostly belong to the same problem)
+    int cached_problem = -1;
+    int64_t cached_nt = 0;
+    auto problem_tiles = [&](int q) -> int64_t {
+        if (q != cached_problem) {
+            cached_nt = prm.problems[q].ntiles;
+            cached_problem = q;
+        }
+        return cached_nt;
+    };
+
+    // neighbour flags of ticket t: three independent relaxed loads, then one
+    // acquire fence (instead of three acquire loads in a row)
+    auto ready = [&](long long t) -> bool {
+        if (prm.span >= 0) return true;
+        const int k = (int)(t / prm.ntiles);
+        if (k == 0) return true;
+        const int tile = (int)(t % prm.ntiles);
+        const int f0 = ld_relaxed(prm.done + tile);
+        const int fl = tile > 0 ? ld_relaxed(prm.done + tile - 1) : k;
+        const int fr = tile + 1 < prm.ntiles ? ld_relaxed(prm.done + tile + 1) : k;
+        const TileDev td = prm.tiles[tile];
+        const int64_t nt = problem_tiles(td.problem);
+        const bool ok = f0 >= k && (td.local == 0 || fl >= k) && (td.local + 1 >= nt || fr >= k);
+        if (ok) fence_acq_rel_gpu();
+        return ok;
+    };
+    auto wait_ready = [&](long long t) -> bool {
+        if (ready(t)) return true;
+        const long long t0 = global_ns();
+        unsigned ns = 32;
+        for (;;) {
+            __nanosleep(ns);
+            if (ns < 1024) ns <<= 1;
+            if (ready(t)) return true;
+            if (*(volatile int*)&prm.err->code != 0) return false;
+            if (global_ns() - t0 > prm.wait_ns) {
+                latch_error(prm.err, kDevTimeoutFlag, (int)(t % prm.ntiles), (int)(t / prm.ntiles), 0);
+                return false;
+            }
+        }
+    };
+
     auto arm = [&](int y, long long t) {
         StageInfo<Real>& si = info[y];
         si.ticket = t;
@@ -517,10 +582,12 @@ __device__ void producer_loop(const SpanParams<Real>& prm, Real* stage, uint64_t
             const int tile = (int)(t % prm.ntiles);
             const int k = (int)(t / prm.ntiles);
             const TileDev td = prm.tiles[tile];
-            const ProblemDev<Real> pr = prm.problems[td.problem];
+            const ProblemDev<Real>& pr = prm.problems[td.problem];
             const int np = td.probe_end - td.probe_begin;
             const int64_t gj0 = (int64_t)td.local * prm.core - prm.H;
             const int64_t n0 = (int64_t)k * prm.S;
+            // the window first: the copy is in flight while the stage's record is written
+            issue_load_tx<Real, W>(prm, t, stage + y * 2 * W, &full_bar[y]);
             si.pr = pr;
             si.td = td;
             si.gj0 = gj0;
@@ -532,55 +599,78 @@ __device__ void producer_loop(const SpanParams<Real>& prm, Real* stage, uint64_t
             si.edge = (gj0 <= 0) || (gj0 + W - 1 >= pr.nx - 1);
             if (np > 0 && np <= kTileProbes)
                 for (int q = 0; q < np; ++q) sprobes[y][q] = prm.probes[td.probe_begin + q];
-            issue_load<Real, W>(prm, t, stage + y * 2 * W, &full_bar[y]);
-        } else {
-            mbar_arrive(&full_bar[y]);
         }
+        // the stage's record is complete before the phase can be observed
+        // (complete_tx needs this arrival too)
+        mbar_arrive(&full_bar[y]);
         fpar ^= 1u << y;
         armed |= 1u << y;
     };
+    auto store_core = [&](int y) {
+        const StageInfo<Real>& si = info[y];
+        const int64_t dst = si.pr.base + (int64_t)si.td.local * prm.core;
+        const uint32_t bytes = (uint32_t)prm.core * sizeof(Real);
+        Real* su = stage + y * 2 * W;
+        bulk_store(span_state(prm, 0, si.k + 1) + dst, su + prm.H, bytes);
+        bulk_store(span_state(prm, 1, si.k + 1) + dst, su + W + prm.H, bytes);
+        bulk_commit();
+    };
 
+    // Stage y holds ticket t (being computed), stage y ^ 1 ticket tn (armed,
+    // or waiting for its neighbours).  The producer never waits for the
+    // neighbours of a ticket while it holds an unpublished older tile.
     int y = 0;
     long long t = grab_ticket(prm, it++);
-    if (t >= 0 && !wait_deps(prm, t)) t = -1;
+    if (t >= 0 && !wait_ready(t)) t = -1;
     arm(0, t);
+    long long tn = -1;
+    bool tn_armed = true;
+    if (t >= 0) {
+        tn = grab_ticket(prm, it++);
+        tn_armed = tn < 0 || ready(tn);
+        if (tn_armed) arm(1, tn);
+    }
     while (t >= 0) {
-        // prefetch the next ticket into the other stage when its neighbours are done
-        const long long tn = grab_ticket(prm, it++);
-        bool next_armed = false;
-        if (tn < 0 || deps_ready(prm, tn)) {
-            arm(y ^ 1, tn);
-            next_armed = true;
-        }
-        // the compute warps hand stage y back
+        // the ticket after tn, fetched now so that the atomic's latency overlaps the compute of t
+        const long long tnn = tn >= 0 ? grab_ticket(prm, it++) : -1;
         if (!mbar_wait_backoff(&empty_bar[y], (epar >> y) & 1u, prm.wait_ns, &prm.err->code)) {
             latch_error(prm.err, kDevTimeoutLoad, (int)(t % prm.ntiles), (int)(t / prm.ntiles), 0);
-            if (!next_armed) arm(y ^ 1, -1);
+            if (!tn_armed) arm(y ^ 1, -1);
             break;
         }
         epar ^= 1u << y;
-        // select + update: store the core, publish once the store has landed
-        {
-            const StageInfo<Real>& si = info[y];
-            const int64_t dst = si.pr.base + (int64_t)si.td.local * prm.core;
-            const uint32_t bytes = (uint32_t)prm.core * sizeof(Real);
-            Real* su = stage + y * 2 * W;
-            bulk_store(span_state(prm, 0, si.k + 1) + dst, su + prm.H, bytes);
-            bulk_store(span_state(prm, 1, si.k + 1) + dst, su + W + prm.H, bytes);
-            bulk_commit();
+        store_core(y);  // select + update of tile t
+        bool published = false;
+        if (!tn_armed) {
+            // tn may need the tile just computed: publish it, then wait for tn's neighbours
             bulk_wait_all();
             publish(prm, t);
-        }
-        if (!next_armed) {
-            // the next ticket may need the tile just published
-            if (wait_deps(prm, tn)) {
-                arm(y ^ 1, tn);
-            } else {
+            published = true;
+            if (!wait_ready(tn)) {
                 arm(y ^ 1, -1);
                 break;
             }
+            arm(y ^ 1, tn);
+            tn_armed = true;
+        }
+        if (tn < 0) {
+            if (!published) {
+                bulk_wait_all();
+                publish(prm, t);
+            }
+            break;
+        }
+        // refill stage y with tnn as soon as the store has read it
+        bulk_wait_read_all();
+        const bool tnn_armed = tnn < 0 || ready(tnn);
+        if (tnn_armed) arm(y, tnn);
+        if (!published) {
+            bulk_wait_all();
+            publish(prm, t);
         }
         t = tn;
+        tn = tnn;
+        tn_armed = tnn_armed;
         y ^= 1;
     }
     bulk_wait_all();
