@@ -95,6 +95,22 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
         smem_to_regs<Real, P>(stage + 1 * W + tid * P, w);
         const Special sp = special_points<Real, P>(gj, nx, -1);
         const bool special = edge && is_special(sp, P);
+        // Dirichlet samples of the span through the warp (warp-uniform choices)
+        WarpChunk<Real> ca{}, cb{};
+        bool wa = false, wb = false;
+        int cbase = 0;
+        if (edge) {
+            wa = __any_sync(kFull, sp.r0 >= 0) && pu.fA != nullptr;
+            wb = __any_sync(kFull, sp.r1 >= 0) && pu.fB != nullptr;
+            if (wa) {
+                ca.c0 = level_sample(pu.fA, 1, at.n0 + lane, prm.T);
+                ca.c1 = level_sample(pu.fA, 1, at.n0 + 32 + lane, prm.T);
+            }
+            if (wb) {
+                cb.c0 = level_sample(pu.fB, 1, at.n0 + lane, prm.T);
+                cb.c1 = level_sample(pu.fB, 1, at.n0 + 32 + lane, prm.T);
+            }
+        }
         for (int s = 0; s < len; ++s) {
             Real lft, rgt;
             exchange<Real, P, NW, BAR>(u, lft, rgt, xch, buf, warp, lane);
@@ -133,12 +149,24 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
                     }
                 }
             }
-            if (step && special) {
-                const int64_t n = at.n0 + s;
-                const Real fa_old = pu.fA ? pu.fA[n] : Real(0), fa_new = pu.fA ? pu.fA[n + 1] : Real(0);
-                const Real fb_old = pu.fB ? pu.fB[n] : Real(0), fb_new = pu.fB ? pu.fB[n + 1] : Real(0);
-                patch_special<Real, FORM, P>(u, w, sp, Real(0), Real(0), fa_old, fa_new, fb_old, fb_new);
+            Real fa_old = Real(0), fa_new = Real(0), fb_old = Real(0), fb_new = Real(0);
+            if (s - cbase == 32) {
+                cbase += 32;
+                ca.c0 = ca.c1;
+                cb.c0 = cb.c1;
+                if (wa) ca.c1 = level_sample(pu.fA, 1, at.n0 + cbase + 32 + lane, prm.T);
+                if (wb) cb.c1 = level_sample(pu.fB, 1, at.n0 + cbase + 32 + lane, prm.T);
             }
+            if (wa) {
+                fa_old = ca.get(s - cbase);
+                fa_new = ca.get(s - cbase + 1);
+            }
+            if (wb) {
+                fb_old = cb.get(s - cbase);
+                fb_new = cb.get(s - cbase + 1);
+            }
+            if (step && special)
+                patch_special<Real, FORM, P>(u, w, sp, Real(0), Real(0), fa_old, fa_new, fb_old, fb_new);
         }
     }
 
@@ -149,6 +177,17 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
     smem_to_regs<Real, P>(stage + 3 * W + tid * P, lw);
     const Special sp = special_points<Real, P>(gj, nx, has_src ? pl.js : -1);
     const bool special = (edge || has_src) && is_special(sp, P);
+    // the source samples (cotangent) of the span through the warp: level m0 + 1 + i
+    WarpChunk<Real> cs{};
+    bool wsrc = false;
+    int sbase = 0;
+    if (has_src) {
+        wsrc = __any_sync(kFull, sp.rs >= 0);
+        if (wsrc) {
+            cs.c0 = level_sample(pl.src, pl.src_stride, at.m0 + 1 + lane, prm.T);
+            cs.c1 = level_sample(pl.src, pl.src_stride, at.m0 + 33 + lane, prm.T);
+        }
+    }
     // core points that are interior grid points: [jlo, jhi)
     const int64_t core_lo = gj0 + prm.H, core_hi = core_lo + prm.core;
     const int64_t jlo = core_lo > 1 ? core_lo : 1;
@@ -168,8 +207,16 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
             const int64_t j = gj + i;
             if (j >= jlo && j < jhi) racc = rfma(l[i], lp[i], racc);
         }
+        Real sval = Real(0);  // src at level m + 1
+        if (wsrc) {
+            if (s - sbase == 32) {
+                sbase += 32;
+                cs.c0 = cs.c1;
+                cs.c1 = level_sample(pl.src, pl.src_stride, at.m0 + sbase + 33 + lane, prm.T);
+            }
+            sval = cs.get(s - sbase);
+        }
         if (special) {
-            const Real sval = sp.rs >= 0 ? pl.src[(m + 1) * pl.src_stride] : Real(0);
             // the increment form adds the source to v before u' = u + v: keep u
             const Real uold = (FORM == kIncrement && sp.rs >= 0) ? select_reg<Real, P>(l, sp.rs) : Real(0);
             leap_step<Real, FORM, P>(l, lw, lft, rgt, c2, kk);

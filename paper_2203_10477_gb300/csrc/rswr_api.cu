@@ -1103,6 +1103,7 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     ap.core = core_a;
     ap.err = e->d_err;
     ap.wait_ns = (long long)(e->wait_s * 1e9);
+    ap.T = T;
     int cur = 0;
     if (use_ws) {
         // all spans, last first, in one launch; the forward state at the start of

@@ -117,6 +117,31 @@ __device__ __forceinline__ void leap_step(Real (&u)[P], Real (&w)[P], Real lft, 
     }
 }
 
+// Per-level samples (boundary waveforms, point sources) of a span held across a
+// warp: lane l keeps the samples of steps base + l (c0) and base + 32 + l (c1);
+// the caller reloads c1 32 steps before it is needed, so the step loop never
+// waits on global memory for them.  Only these two values per stream live
+// across steps.  Every call is made by all lanes of the warp with the same
+// arguments.
+template <typename Real>
+struct WarpChunk {
+    Real c0, c1;
+    // the sample of step base + d, 0 <= d <= 32
+    __device__ __forceinline__ Real get(int d) const
+    {
+        const Real v0 = __shfl_sync(kFull, c0, d & 31);
+        const Real v1 = __shfl_sync(kFull, c1, d & 31);
+        return d < 32 ? v0 : v1;
+    }
+};
+
+// a[level * stride] for 0 <= level <= nmax, else 0
+template <typename Real>
+__device__ __forceinline__ Real level_sample(const Real* a, int64_t stride, int64_t level, int64_t nmax)
+{
+    return (a != nullptr && level >= 0 && level <= nmax) ? a[level * stride] : Real(0);
+}
+
 // Points of a thread that need more than the stencil: the Dirichlet nodes
 // (local index r0 -> j = 0, r1 -> j = nx-1), the point source (rs) and points
 // outside [0, nx) (local indices outside [rlo, rhi]).  -1 = not owned.

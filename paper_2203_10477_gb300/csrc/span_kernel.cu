@@ -225,7 +225,33 @@ __device__ __forceinline__ void predict_tile(const SpanParams<Real>& prm, const 
             }
         }
         Special sp{-1, -1, -1, 0, P - 1};
-        if constexpr (SP) sp = special_points();
+        // boundary and source samples of the span, through the warp (warp-uniform choices):
+        // fA / fB at level n0 + s_begin + i, the source at level n0 + s_begin + i + 1
+        WarpChunk<Real> ca{}, cb{}, cs{};
+        bool wa = false, wb = false, wsrc = false;
+        int cbase = 0;
+        auto reload = [&](int first, bool both) {  // chunk(s) of steps first + lane (+ 32)
+            const int64_t lv = n0 + s_begin + first + lane;
+            if (wa) {
+                if (both) ca.c0 = level_sample(pr.fA, 1, lv, prm.T);
+                ca.c1 = level_sample(pr.fA, 1, lv + 32, prm.T);
+            }
+            if (wb) {
+                if (both) cb.c0 = level_sample(pr.fB, 1, lv, prm.T);
+                cb.c1 = level_sample(pr.fB, 1, lv + 32, prm.T);
+            }
+            if (wsrc) {
+                if (both) cs.c0 = level_sample(pr.src, pr.src_stride, lv + 1, prm.T);
+                cs.c1 = level_sample(pr.src, pr.src_stride, lv + 33, prm.T);
+            }
+        };
+        if constexpr (SP) {
+            sp = special_points();
+            wa = __any_sync(kFull, sp.r0 >= 0) && pr.fA != nullptr;
+            wb = __any_sync(kFull, sp.r1 >= 0) && pr.fB != nullptr;
+            wsrc = __any_sync(kFull, sp.rs >= 0);
+            reload(0, true);
+        }
         if constexpr (KH > 0 && !PR && !SP) {
             // plain interior tile of a warp window: the bare stencil, edges first
             warp_steps_edges_first<Real, FORM, P>(u, w, c2, kk, s_end - s_begin, lane);
@@ -250,15 +276,29 @@ __device__ __forceinline__ void predict_tile(const SpanParams<Real>& prm, const 
                                            prm.probes, n);
             }
             if constexpr (SP) {
-                Real uold_s = Real(0), sval = Real(0);
-                if (sp.rs >= 0) {
-                    sval = pr.src[(n + 1) * pr.src_stride];
-                    if constexpr (FORM == kIncrement) uold_s = select_reg<Real, P>(u, sp.rs);
+                const int d = s - s_begin - cbase;
+                if (d == 32) {
+                    // move to the next chunk; load the one after it
+                    cbase += 32;
+                    ca.c0 = ca.c1;
+                    cb.c0 = cb.c1;
+                    cs.c0 = cs.c1;
+                    reload(cbase, false);
                 }
-                const Real fa_old = pr.fA ? pr.fA[n] : Real(0);
-                const Real fa_new = pr.fA ? pr.fA[n + 1] : Real(0);
-                const Real fb_old = pr.fB ? pr.fB[n] : Real(0);
-                const Real fb_new = pr.fB ? pr.fB[n + 1] : Real(0);
+                const int dd = s - s_begin - cbase;
+                Real uold_s = Real(0), sval = Real(0);
+                Real fa_old = Real(0), fa_new = Real(0), fb_old = Real(0), fb_new = Real(0);
+                if (wsrc) sval = cs.get(dd);  // src at level n + 1
+                if (wa) {
+                    fa_old = ca.get(dd);
+                    fa_new = ca.get(dd + 1);
+                }
+                if (wb) {
+                    fb_old = cb.get(dd);
+                    fb_new = cb.get(dd + 1);
+                }
+                if constexpr (FORM == kIncrement)
+                    if (sp.rs >= 0) uold_s = select_reg<Real, P>(u, sp.rs);
                 leap_step<Real, FORM, P>(u, w, lft, rgt, c2, kk);
                 patch_special<Real, FORM, P>(u, w, sp, uold_s, sval, fa_old, fa_new, fb_old, fb_new);
             } else {
@@ -818,6 +858,7 @@ const Entry* table(int* n)
         make_entry<float, kIncrement, 16, 128, 8, 4>(),
         make_entry<float, kIncrement, 16, 128, 0, 4>(),
         // FP32 canonical
+        make_entry_ws<float, kCanonical, 24, 128, 32, 4>(),
         make_entry<float, kCanonical, 16, 128, 0, 4>(),
         // FP64 canonical (the FP64 default form)
         make_entry_ws<double, kCanonical, 8, 128, 0, 4>(),

@@ -129,7 +129,7 @@ def test_random_state_bitwise(R, oracle_mod, dtype, form, case, mode):
         assert_bitwise(host(out["traces"]), rs["traces"], "traces")
 
 
-@pytest.mark.parametrize("dtype,form", [(F64, CAN), (F32, INC)])
+@pytest.mark.parametrize("dtype,form", [(F64, CAN), (F32, INC), (F32, CAN), (F64, INC)])
 def test_every_variant_and_span_gives_identical_bits(R, oracle_mod, dtype, form):
     nx, N, ov, T = 30011, 5, 48, 203
     dt = 0.85 / (nx - 1)
@@ -143,7 +143,7 @@ def test_every_variant_and_span_gives_identical_bits(R, oracle_mod, dtype, form)
                               q0=q0.astype(dt_))
     plan = R.Plan(0.0, 1.0, 1.0, nx, dt, N, ov, dtype=dtype, form=form)
     vs = [v for v in R.variants() if v["dtype"] == dtype and v["form"] == form]
-    assert len(vs) >= 2
+    assert len(vs) >= 1
     for v in vs:
         for S in (1, 7, 16, ov // 2):
             if v["max_span"] and S > v["max_span"]:
