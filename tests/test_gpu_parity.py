@@ -198,6 +198,40 @@ def test_short_and_ragged_spans(R, oracle_mod, T):
     assert_bitwise(host(out["recv"]), ref["rec"][0], "receiver")
 
 
+@pytest.mark.parametrize("dtype,form", [(F64, CAN), (F64, INC), (F32, INC), (F32, CAN)])
+def test_spans_longer_than_a_sample_chunk(R, oracle_mod, dtype, form):
+    """Spans of 64 steps: the boundary samples a warp holds are reloaded inside
+    the span (every 32 steps), at both Dirichlet ends."""
+    nx, N, ov, T = 5003, 3, 128, 300
+    dt = 0.9 / (nx - 1)
+    fA = inputs.ramped_sine(T, dt, freq=40.0) + 0.3
+    fB = 0.7 * inputs.ramped_sine(T, dt, freq=23.0) - 0.1
+    plan = R.Plan(0.0, 1.0, 1.0, nx, dt, N, ov, dtype=dtype, form=form)
+    plan.set_span(64)
+    assert plan.info()["span_steps"] == 64
+    out = plan.run(fA, fB, T, traces=True, j_r=4000)
+    plan.check()
+    ref = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, fB, form=ORACLE_FORM[form], prec=prec(dtype), rec_j=[4000])
+    assert_bitwise(host(out["u"]), ref["u"], "u")
+    assert_bitwise(host(out["w"]), ref["w"], "w")
+    assert_bitwise(host(out["recv"]), ref["rec"][0], "receiver")
+
+
+def test_adjoint_source_with_long_spans(R, oracle_mod):
+    """The adjoint source (cotangent) through the span kernel with 64-step spans."""
+    nx, N, ov, T, jr = 3001, 2, 128, 700, 1500
+    a = 1.0
+    dt = 0.9 / (nx - 1)
+    g = inputs.lowpass_noise(T, seed=31)
+    w = inputs.rng(32).standard_normal(T + 1)
+    plan = R.Plan(0.0, 1.0, a, nx, dt, N, ov, dtype=F64)
+    plan.set_span(64)
+    res = plan.adjoint(g, None, T, jr, w)
+    plan.check()
+    ref = oracle_mod.adjoint(nx, T, a, dt, g, np.zeros(T + 1), jr, w)
+    assert_bitwise(host(res["grad_fA"]), ref["dg"], "grad_fA with 64-step spans")
+
+
 def test_smallest_grids(R, oracle_mod):
     for nx, N, ov in ((3, 1, 2), (4, 2, 2), (9, 2, 4), (64, 4, 16)):
         T = 40
