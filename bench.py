@@ -327,10 +327,10 @@ def e2e_run(torch, plan, p, steps):
     return ms, h2d, d2h
 
 
-def profile_case(which: str, variant=None, span=None, full=False) -> None:
+def profile_case(which: str, variant=None, span=None, full=False, log2_nx=22) -> None:
     """The bench workload (full = True) or its small version for detailed
-    captures: nx = 2^22, 256 subdomains (the bench's subdomain length of 16384
-    points, so the same share of tiles carries interface probes) and 1280 steps
+    captures: nx = 2^log2_nx (default 2^22), subdomains of the bench's length of
+    16384 points (so the same share of tiles carries interface probes) and 1280 steps
     (40 spans of 32, so the fill and drain of the span pipeline are a small
     part); four state arrays of 32 MiB (FP64) / 16 MiB (FP32), so DRAM counters
     still see traffic beyond L2.  Runs the workload twice (the first run warms
@@ -359,8 +359,8 @@ def profile_case(which: str, variant=None, span=None, full=False) -> None:
     if full:
         p = inputs.c2()
     else:
-        p = inputs.c2(T=1280, nx=1 << 22)
-        p = dataclasses.replace(p, n_sub=p.nx // 16384)
+        p = inputs.c2(T=1280, nx=1 << log2_nx)
+        p = dataclasses.replace(p, n_sub=max(1, p.nx // 16384))
     plan = rswr.Plan.from_problem(p, dtype=rswr.F64 if which == "f64" else rswr.F32)
     if span is not None:
         plan.set_span(span)
@@ -541,12 +541,14 @@ def main():
     ap.add_argument("--profile-case", choices=["f64", "f32", "adj64", "adj32"], default=None,
                     help="run the small profiling case (nx=2^22, 1280 steps) twice and exit (for ncu)")
     ap.add_argument("--variant", type=int, default=None, help="kernel variant of the profiling case")
+    ap.add_argument("--profile-log2-nx", type=int, default=22,
+                    help="grid of the profiling case: 2^N points (24 = the bench grid)")
     ap.add_argument("--span", type=int, default=None, help="steps per span of the profiling case")
     ap.add_argument("--full", action="store_true", help="profiling case at the bench's full size")
     args = ap.parse_args()
 
     if args.profile_case:
-        profile_case(args.profile_case, args.variant, args.span, args.full)
+        profile_case(args.profile_case, args.variant, args.span, args.full, args.profile_log2_nx)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -21,6 +21,8 @@
 // (block reduction in a fixed order; the host sums tiles and spans in a fixed
 // order too, so the result is deterministic).
 
+#include <algorithm>
+
 #include "rswr_internal.h"
 #include "span_common.cuh"
 
@@ -521,25 +523,40 @@ __global__ void adj_init_kernel(Real* l0, Real* l1, const ProblemDev<Real>* prob
     l1[pr.base + pr.js] = form == kCanonical ? Real(0) : w;  // lambda^{T+1} = 0 / increment
 }
 
-// One block per problem; fixed-order sum over (span, tile).
-__global__ void adj_reduce_kernel(const double* partial, int64_t nspans, int64_t ntiles, const int64_t* tile0,
-                                  const int64_t* tcount, const double* scale, double* out)
+// dL/da per problem in a fixed order, in two stages.  Stage 1: block b of
+// problem p sums the partials of spans [b nspans / B, (b + 1) nspans / B) (each
+// thread a fixed strided set of tiles, then a fixed tree); stage 2: one thread
+// per problem adds the B block sums in order and scales.
+constexpr int kRedThreads = 256;
+
+__global__ void adj_reduce_stage1(const double* partial, int64_t nspans, int64_t ntiles, const int64_t* tile0,
+                                  const int64_t* tcount, int B, double* tmp)
 {
-    const int p = blockIdx.x;
-    __shared__ double red[256];
+    const int p = (int)(blockIdx.x / B), b = (int)(blockIdx.x % B);
+    __shared__ double red[kRedThreads];
+    const int64_t tc = tcount[p], t0 = tile0[p];
+    const int64_t k0 = (int64_t)b * nspans / B, k1 = (int64_t)(b + 1) * nspans / B;
     double acc = 0.0;
-    const int64_t n = nspans * tcount[p];
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const int64_t k = i / tcount[p], t = i % tcount[p];
-        acc += partial[k * ntiles + tile0[p] + t];
+    for (int64_t k = k0; k < k1; ++k) {
+        const double* row = partial + k * ntiles + t0;
+        for (int64_t t = threadIdx.x; t < tc; t += kRedThreads) acc += row[t];
     }
     red[threadIdx.x] = acc;
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
         if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[p] = red[0] * scale[p];
+    if (threadIdx.x == 0) tmp[(int64_t)p * B + b] = red[0];
+}
+
+__global__ void adj_reduce_stage2(const double* tmp, int B, const double* scale, double* out, int nprob)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nprob) return;
+    double t = 0.0;
+    for (int b = 0; b < B; ++b) t += tmp[(int64_t)p * B + b];
+    out[p] = t * scale[p];
 }
 
 struct AEntry {
@@ -703,10 +720,22 @@ cudaError_t adj_init_launch(int dtype, int form, void* l0, void* l1, const void*
     return cudaGetLastError();
 }
 
-cudaError_t adj_reduce_launch(const double* partial, int64_t nspans, int64_t ntiles, const int64_t* tile0,
-                              const int64_t* tcount, const double* scale, double* out, int nprob, cudaStream_t s)
+int adj_reduce_blocks(int64_t nspans, int nprob)
 {
-    adj_reduce_kernel<<<nprob, 256, 0, s>>>(partial, nspans, ntiles, tile0, tcount, scale, out);
+    // enough blocks to fill the GPU for one large problem, few for many problems
+    int64_t b = std::min<int64_t>(nspans, 256);
+    while (b > 1 && b * nprob > 4096) b /= 2;
+    return (int)std::max<int64_t>(b, 1);
+}
+
+cudaError_t adj_reduce_launch(const double* partial, int64_t nspans, int64_t ntiles, const int64_t* tile0,
+                              const int64_t* tcount, const double* scale, double* out, int nprob, double* tmp,
+                              cudaStream_t s)
+{
+    const int B = adj_reduce_blocks(nspans, nprob);
+    adj_reduce_stage1<<<(unsigned)B * (unsigned)nprob, kRedThreads, 0, s>>>(partial, nspans, ntiles, tile0, tcount,
+                                                                            B, tmp);
+    adj_reduce_stage2<<<(nprob + 127) / 128, 128, 0, s>>>(tmp, B, scale, out, nprob);
     return cudaGetLastError();
 }
 

@@ -923,7 +923,8 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     const size_t b_probes = up(sizeof(ProbeDev<Real>) * np);
     const size_t b_red = up(sizeof(int64_t) * 2 * np + sizeof(double) * np);
     const size_t b_done = up(sizeof(int) * std::max<int64_t>(ntf, nta));
-    const size_t need = b_states + b_partial + b_tiles + b_prob + b_probes + b_red + b_done;
+    const size_t b_rtmp = up(sizeof(double) * (size_t)adj_reduce_blocks(std::max<int64_t>(nspans, 1), np) * np);
+    const size_t need = b_states + b_partial + b_tiles + b_prob + b_probes + b_red + b_done + b_rtmp;
     if (need > e->adj_mem_cap) {
         RSWR_CUDA(cudaStreamSynchronize(s));
         cudaFree(e->adj_mem);
@@ -954,6 +955,8 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     double* d_scale = reinterpret_cast<double*>(d_tc + np);
     q += b_red;
     int* d_done = reinterpret_cast<int*>(q);
+    q += b_done;
+    double* d_rtmp = reinterpret_cast<double*>(q);
     const int64_t CK0 = 0, SG0 = nck, WK0 = nck + C, LM0 = nck + C + 2;
 
     // host tables
@@ -1156,7 +1159,7 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     }
     if (grad_a) {
         if (nspans > 0)
-            RSWR_CUDA(adj_reduce_launch(partial, nspans, nta, d_t0, d_tc, d_scale, grad_a, np, s));
+            RSWR_CUDA(adj_reduce_launch(partial, nspans, nta, d_t0, d_tc, d_scale, grad_a, np, d_rtmp, s));
         else
             RSWR_CUDA(cudaMemsetAsync(grad_a, 0, sizeof(double) * np, s));
     }

@@ -190,9 +190,12 @@ int adj_ws_window(int dtype, int form);  // points per CTA window of the persist
 // lambda at level 1 of the reversed-time sweep: wbar[T] at j_r (interior receivers only)
 cudaError_t adj_init_launch(int dtype, int form, void* l0, void* l1, const void* prob_l, int nprob,
                             const void* wbar, int64_t T, cudaStream_t s);
-// dL/da[p] = 2 c2_p / a_p * sum of the partials of problem p's tiles over all spans
+// dL/da[p] = 2 c2_p / a_p * sum of the partials of problem p's tiles over all
+// spans, in a fixed order; tmp holds adj_reduce_blocks(nspans, nprob) * nprob doubles
+int adj_reduce_blocks(int64_t nspans, int nprob);
 cudaError_t adj_reduce_launch(const double* partial, int64_t nspans, int64_t ntiles, const int64_t* tile0,
-                              const int64_t* tcount, const double* scale, double* out, int nprob, cudaStream_t s);
+                              const int64_t* tcount, const double* scale, double* out, int nprob, double* tmp,
+                              cudaStream_t s);
 
 // paper_kernel.cu
 cudaError_t paper_iface_launch(int dtype, const void* params, int n_iface, size_t smem, cudaStream_t s);
