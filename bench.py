@@ -343,15 +343,20 @@ def profile_case(which: str, variant=None, span=None, full=False, log2_nx=22) ->
 
     build.build()
     if which in ("adj64", "adj32"):
-        # the c4 gradient workload (dL/dfA and dL/da), run twice
-        p = inputs.c4(j_r=4000)
+        # the c4 gradient workload (dL/dfA and dL/da), run twice; a smaller grid
+        # (log2_nx < 20) scales the steps with it
+        if log2_nx >= 20:
+            p = inputs.c4(j_r=4000)
+        else:
+            sh = 20 - log2_nx
+            p = inputs.c4(T=8192 >> sh, nx=1 << log2_nx, j_r=4000 >> sh)
         dtype = rswr.F64 if which == "adj64" else rswr.F32
         td = torch.float64 if dtype == rswr.F64 else torch.float32
         plan = rswr.Plan.from_problem(p, dtype=dtype)
         fA = torch.as_tensor(p.fA, device="cuda").to(td)
         w = torch.as_tensor(inputs.lowpass_noise(p.T, seed=4), device="cuda").to(td)
         for _ in range(2):
-            plan.adjoint(fA, None, p.T, 4000, w, want_a=True)
+            plan.adjoint(fA, None, p.T, p.meta["j_r"], w, want_a=True)
         torch.cuda.synchronize()
         plan.check()
         print(json.dumps({"profile_case": which, "nx": p.nx, "T": p.T, "info": plan.info()}))
@@ -541,14 +546,18 @@ def main():
     ap.add_argument("--profile-case", choices=["f64", "f32", "adj64", "adj32"], default=None,
                     help="run the small profiling case (nx=2^22, 1280 steps) twice and exit (for ncu)")
     ap.add_argument("--variant", type=int, default=None, help="kernel variant of the profiling case")
-    ap.add_argument("--profile-log2-nx", type=int, default=22,
-                    help="grid of the profiling case: 2^N points (24 = the bench grid)")
+    ap.add_argument("--profile-log2-nx", type=int, default=None,
+                    help="grid of the profiling case: 2^N points (default 22; 24 = the bench grid; "
+                         "adj64/adj32: default 20 = the c4 grid)")
     ap.add_argument("--span", type=int, default=None, help="steps per span of the profiling case")
     ap.add_argument("--full", action="store_true", help="profiling case at the bench's full size")
     args = ap.parse_args()
 
     if args.profile_case:
-        profile_case(args.profile_case, args.variant, args.span, args.full, args.profile_log2_nx)
+        lg = args.profile_log2_nx
+        if lg is None:
+            lg = 20 if args.profile_case in ("adj64", "adj32") else 22
+        profile_case(args.profile_case, args.variant, args.span, args.full, lg)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -89,6 +89,13 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
     const bool edge = (gj0 <= 0) || (gj0 + W - 1 >= nx - 1);
     const bool has_src = pl.js >= 0 && pl.js >= gj0 && pl.js < gj0 + W;
     const int len = at.len;
+    // layout of the Laplacian store within a level: FP32 point-major across the
+    // threads (consecutive threads touch consecutive words: no bank conflicts);
+    // FP64 thread-major (a thread's points in 16-byte pieces; the FP64 pipe,
+    // not shared memory, bounds this kernel)
+    constexpr bool kPointMajor = sizeof(Real) == 4;
+    constexpr int lap_stride = kPointMajor ? NT : 1;
+    const int lap_base = kPointMajor ? tid : tid * P;
 
     // ---- u phase: levels n0 .. n0+len-1, Laplacians of every level to shared memory
     {
@@ -117,7 +124,7 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
             Real lft, rgt;
             exchange<Real, P, NW, BAR>(u, lft, rgt, xch, buf, warp, lane);
             buf ^= 1;
-            Real* lp = laps + s * W + tid * P;
+            Real* lp = laps + s * W + lap_base;  // point i of this thread at lp[i * lap_stride]
             const bool step = s + 1 < len;
             // one pass: the Laplacian of this level (from the step's own neighbour
             // sum, (uL + uR) - 2u = fma(-2, u, uL + uR) exactly) and the step
@@ -128,7 +135,7 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
                     const Real uc = u[i];
                     const Real ur = i < P - 1 ? u[i + 1] : rgt;
                     const Real sum = radd(ul, ur);
-                    lp[i] = rfma(Real(-2), uc, sum);
+                    lp[i * lap_stride] = rfma(Real(-2), uc, sum);
                     if (step) {
                         u[i] = rfma(c2, sum, rfma(kk, uc, -w[i]));
                         w[i] = uc;
@@ -143,7 +150,7 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
                     const Real d = rsub(ur, u[i]);
                     const Real lap = rsub(d, d_prev);
                     d_prev = d;
-                    lp[i] = lap;
+                    lp[i * lap_stride] = lap;
                     if (step) {
                         const Real v = rfma(c2, lap, w[i]);
                         w[i] = v;
@@ -194,6 +201,9 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
     const int64_t core_lo = gj0 + prm.H, core_hi = core_lo + prm.core;
     const int64_t jlo = core_lo > 1 ? core_lo : 1;
     const int64_t jhi = core_hi < nx - 1 ? core_hi : nx - 1;
+    // the same range in this thread's register indices
+    const int ilo = (int)(jlo - gj <= 0 ? 0 : (jlo - gj >= P ? P : jlo - gj));
+    const int ihi = (int)(jhi - gj <= 0 ? 0 : (jhi - gj >= P ? P : jhi - gj));
     for (int s = 0; s < len; ++s) {
         Real lft, rgt;
         exchange<Real, P, NW, BAR>(l, lft, rgt, xch, buf, warp, lane);
@@ -203,12 +213,10 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
             record_probes<Real, P>(l, lft, rgt, wabs, tid * P, 0, P, at.td.probe_begin, at.td.probe_end, prm.probes,
                                    m);
         // each thread reads the Laplacians of its own points only
-        const Real* lp = laps + (len - 1 - s) * W + tid * P;
+        const Real* lp = laps + (len - 1 - s) * W + lap_base;
 #pragma unroll
-        for (int i = 0; i < P; ++i) {
-            const int64_t j = gj + i;
-            if (j >= jlo && j < jhi) racc = rfma(l[i], lp[i], racc);
-        }
+        for (int i = 0; i < P; ++i)
+            if (i >= ilo && i < ihi) racc = rfma(l[i], lp[i * lap_stride], racc);
         Real sval = Real(0);  // src at level m + 1
         if (wsrc) {
             if (s - sbase == 32) {
@@ -259,6 +267,7 @@ __global__ void __launch_bounds__(NT) adjoint_kernel(const __grid_constant__ Adj
     Real* xch = laps + SA * W;                        // [2][NW][2]
     __shared__ __align__(8) uint64_t bar;
     __shared__ double red[NW];
+    __shared__ __align__(16) ProblemDev<Real> s_pu, s_pl;
 
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -273,14 +282,16 @@ __global__ void __launch_bounds__(NT) adjoint_kernel(const __grid_constant__ Adj
     for (int64_t tile = blockIdx.x; tile < prm.ntiles; tile += gridDim.x) {
         AdjTile<Real> at;
         at.td = prm.tiles[tile];
-        at.pu = &prm.prob_u[at.td.problem];
-        at.pl = &prm.prob_l[at.td.problem];
+        at.pu = &s_pu;  // shared-memory copies, written by thread 0 below
+        at.pl = &s_pl;
         at.gj0 = (int64_t)at.td.local * prm.core - prm.H;
         at.n0 = prm.n0;
         at.m0 = prm.m0;
         at.len = prm.len;
-        const int64_t wabs = at.pu->base + at.gj0;
         if (tid == 0) {
+            s_pu = prm.prob_u[at.td.problem];
+            s_pl = prm.prob_l[at.td.problem];
+            const int64_t wabs = s_pu.base + at.gj0;
             constexpr uint32_t bytes = W * sizeof(Real);
             bulk_wait_read_all();  // the previous tile's store has read the stage
             fence_proxy_async_global();
@@ -325,9 +336,13 @@ __global__ void __launch_bounds__(NT) adjoint_kernel(const __grid_constant__ Adj
 // adjoint core and publishes; the compute threads run adj_tile with a named
 // barrier among themselves (barrier 1) and write the tile's partial sum.
 
+template <typename Real>
 struct AdjStage {
-    long long ticket;  // -1: no more work
-    int kp;            // processing index (span K = nspans - 1 - kp)
+    ProblemDev<Real> pu;  // copies of the tile's forward and adjoint problem records
+    ProblemDev<Real> pl;
+    TileDev td;
+    long long ticket;     // -1: no more work
+    int kp;               // processing index (span K = nspans - 1 - kp)
     int tile;
     int64_t gj0, n0, m0;
     int len;
@@ -336,7 +351,7 @@ struct AdjStage {
 
 template <typename Real, int W>
 __device__ void adj_producer(const AdjParams<Real>& prm, Real* stage, uint64_t* full_bar, uint64_t* empty_bar,
-                             AdjStage* info)
+                             AdjStage<Real>* info)
 {
     const unsigned long long total = (unsigned long long)prm.nspans * (unsigned long long)prm.ntiles;
     auto grab = [&]() -> long long {
@@ -344,16 +359,25 @@ __device__ void adj_producer(const AdjParams<Real>& prm, Real* stage, uint64_t* 
         const unsigned long long t = atomicAdd(prm.ticket, 1ull);
         return t < total ? (long long)t : -1;
     };
+    // tile count of the problem of the last ticket looked at
+    int cached_problem = -1;
+    int64_t cached_nt = 0;
+    // neighbour flags: three independent relaxed loads, then one acquire fence
     auto ready = [&](long long t) -> bool {
         const int kp = (int)(t / prm.ntiles);
         if (kp == 0) return true;
         const int tile = (int)(t % prm.ntiles);
+        const int f0 = ld_relaxed(prm.done + tile);
+        const int fl = tile > 0 ? ld_relaxed(prm.done + tile - 1) : kp;
+        const int fr = tile + 1 < prm.ntiles ? ld_relaxed(prm.done + tile + 1) : kp;
         const TileDev td = prm.tiles[tile];
-        const int64_t nt = prm.prob_l[td.problem].ntiles;
-        if (ld_acquire(prm.done + tile) < kp) return false;
-        if (td.local > 0 && ld_acquire(prm.done + tile - 1) < kp) return false;
-        if (td.local + 1 < nt && ld_acquire(prm.done + tile + 1) < kp) return false;
-        return true;
+        if (td.problem != cached_problem) {
+            cached_nt = prm.prob_l[td.problem].ntiles;
+            cached_problem = td.problem;
+        }
+        const bool ok = f0 >= kp && (td.local == 0 || fl >= kp) && (td.local + 1 >= cached_nt || fr >= kp);
+        if (ok) fence_acq_rel_gpu();
+        return ok;
     };
     auto wait_ready = [&](long long t) -> bool {
         if (ready(t)) return true;
@@ -373,7 +397,7 @@ __device__ void adj_producer(const AdjParams<Real>& prm, Real* stage, uint64_t* 
     uint32_t fpar = 0u, epar = 0u, armed = 0u;
     constexpr uint32_t bytes = W * sizeof(Real);
     auto arm = [&](int y, long long t) {
-        AdjStage& si = info[y];
+        AdjStage<Real>& si = info[y];
         si.ticket = t;
         if (t >= 0) {
             const int kp = (int)(t / prm.ntiles);
@@ -382,6 +406,14 @@ __device__ void adj_producer(const AdjParams<Real>& prm, Real* stage, uint64_t* 
             const TileDev td = prm.tiles[tile];
             const int64_t gj0 = (int64_t)td.local * prm.core - prm.H;
             const int64_t wabs = prm.prob_u[td.problem].base + gj0;
+            Real* st = stage + y * 4 * W;
+            // the windows first (bytes expected, no arrival yet), then the stage record
+            fence_proxy_async_global();
+            mbar_expect_tx(&full_bar[y], 4 * bytes);
+            bulk_load(st + 0 * W, prm.uck0 + K * prm.ck_stride + wabs, bytes, &full_bar[y]);
+            bulk_load(st + 1 * W, prm.uck1 + K * prm.ck_stride + wabs, bytes, &full_bar[y]);
+            bulk_load(st + 2 * W, prm.lq0[kp & 1] + wabs, bytes, &full_bar[y]);
+            bulk_load(st + 3 * W, prm.lq1[kp & 1] + wabs, bytes, &full_bar[y]);
             const int64_t n0 = K * prm.SA;
             const int len = (int)((prm.T - n0 < prm.SA) ? (prm.T - n0) : prm.SA);
             si.kp = kp;
@@ -390,61 +422,86 @@ __device__ void adj_producer(const AdjParams<Real>& prm, Real* stage, uint64_t* 
             si.n0 = n0;
             si.len = len;
             si.m0 = prm.T - (n0 + len - 1);
-            Real* st = stage + y * 4 * W;
-            fence_proxy_async_global();
-            mbar_arrive_expect_tx(&full_bar[y], 4 * bytes);
-            bulk_load(st + 0 * W, prm.uck0 + K * prm.ck_stride + wabs, bytes, &full_bar[y]);
-            bulk_load(st + 1 * W, prm.uck1 + K * prm.ck_stride + wabs, bytes, &full_bar[y]);
-            bulk_load(st + 2 * W, prm.lq0[kp & 1] + wabs, bytes, &full_bar[y]);
-            bulk_load(st + 3 * W, prm.lq1[kp & 1] + wabs, bytes, &full_bar[y]);
-        } else {
-            mbar_arrive(&full_bar[y]);
+            si.td = td;
+            si.pu = prm.prob_u[td.problem];
+            si.pl = prm.prob_l[td.problem];
         }
+        mbar_arrive(&full_bar[y]);  // the one arrival of the phase, after the record
         fpar ^= 1u << y;
         armed |= 1u << y;
     };
+    auto store_core = [&](int y) {
+        const AdjStage<Real>& si = info[y];
+        const int64_t dst = si.pu.base + (int64_t)si.td.local * prm.core;
+        const uint32_t cbytes = (uint32_t)prm.core * sizeof(Real);
+        Real* st = stage + y * 4 * W;
+        const int out = (si.kp + 1) & 1;
+        bulk_store(prm.lq0[out] + dst, st + 2 * W + prm.H, cbytes);
+        bulk_store(prm.lq1[out] + dst, st + 3 * W + prm.H, cbytes);
+        bulk_commit();
+    };
+    auto publish = [&](int y) {
+        fence_proxy_async_global();
+        __threadfence();
+        st_release(prm.done + info[y].tile, info[y].kp + 1);
+    };
 
+    // As the span kernel's producer: stage y holds t (being computed), stage
+    // y ^ 1 holds tn (armed, or waiting for its neighbours); the producer never
+    // waits for a ticket's neighbours while it holds an unpublished older tile.
     int y = 0;
     long long t = grab();
     if (t >= 0 && !wait_ready(t)) t = -1;
     arm(0, t);
+    long long tn = -1;
+    bool tn_armed = true;
+    if (t >= 0) {
+        tn = grab();
+        tn_armed = tn < 0 || ready(tn);
+        if (tn_armed) arm(1, tn);
+    }
     while (t >= 0) {
-        const long long tn = grab();
-        bool next_armed = false;
-        if (tn < 0 || ready(tn)) {
-            arm(y ^ 1, tn);
-            next_armed = true;
-        }
+        const long long tnn = tn >= 0 ? grab() : -1;
         if (!mbar_wait_backoff(&empty_bar[y], (epar >> y) & 1u, prm.wait_ns, &prm.err->code)) {
             latch_error(prm.err, kDevTimeoutLoad, (int)(t % prm.ntiles), (int)(t / prm.ntiles), 1);
-            if (!next_armed) arm(y ^ 1, -1);
+            if (!tn_armed) arm(y ^ 1, -1);
             break;
         }
         epar ^= 1u << y;
-        {
-            const AdjStage& si = info[y];
-            const TileDev td = prm.tiles[si.tile];
-            const int64_t dst = prm.prob_u[td.problem].base + (int64_t)td.local * prm.core;
-            const uint32_t cbytes = (uint32_t)prm.core * sizeof(Real);
-            Real* st = stage + y * 4 * W;
-            const int out = (si.kp + 1) & 1;
-            bulk_store(prm.lq0[out] + dst, st + 2 * W + prm.H, cbytes);
-            bulk_store(prm.lq1[out] + dst, st + 3 * W + prm.H, cbytes);
-            bulk_commit();
+        store_core(y);
+        bool published = false;
+        if (!tn_armed) {
             bulk_wait_all();
-            fence_proxy_async_global();
-            __threadfence();
-            st_release(prm.done + si.tile, si.kp + 1);
-        }
-        if (!next_armed) {
-            if (wait_ready(tn)) {
-                arm(y ^ 1, tn);
-            } else {
+            publish(y);
+            published = true;
+            if (!wait_ready(tn)) {
                 arm(y ^ 1, -1);
                 break;
             }
+            arm(y ^ 1, tn);
+            tn_armed = true;
+        }
+        if (tn < 0) {
+            if (!published) {
+                bulk_wait_all();
+                publish(y);
+            }
+            break;
+        }
+        bulk_wait_read_all();
+        // stage y's record (tile, kp) is still needed by publish: keep it until then
+        const int pub_tile = info[y].tile, pub_kp = info[y].kp;
+        const bool tnn_armed = tnn < 0 || ready(tnn);
+        if (tnn_armed) arm(y, tnn);
+        if (!published) {
+            bulk_wait_all();
+            fence_proxy_async_global();
+            __threadfence();
+            st_release(prm.done + pub_tile, pub_kp + 1);
         }
         t = tn;
+        tn = tnn;
+        tn_armed = tnn_armed;
         y ^= 1;
     }
     bulk_wait_all();
@@ -463,7 +520,7 @@ __global__ void __launch_bounds__(NT + 32) adjoint_kernel_ws(const __grid_consta
     Real* xch = laps + SA * W;                        // [2][NW][2]
     __shared__ __align__(8) uint64_t full_bar[2];
     __shared__ __align__(8) uint64_t empty_bar[2];
-    __shared__ AdjStage s_info[2];
+    __shared__ __align__(16) AdjStage<Real> s_info[2];
     __shared__ double red[NW];
 
     const int tid = threadIdx.x;
@@ -489,12 +546,12 @@ __global__ void __launch_bounds__(NT + 32) adjoint_kernel_ws(const __grid_consta
         fpar ^= 1u << y;
         if (!ok) latch_error(prm.err, kDevTimeoutLoad, -1, -1, 1);
         if (block_sync_or<NT>(!ok)) break;  // one decision for all compute threads
-        const AdjStage& si = s_info[y];
+        const AdjStage<Real>& si = s_info[y];
         if (si.ticket < 0) break;
         AdjTile<Real> at;
-        at.td = prm.tiles[si.tile];
-        at.pu = &prm.prob_u[at.td.problem];
-        at.pl = &prm.prob_l[at.td.problem];
+        at.td = si.td;
+        at.pu = &si.pu;  // shared-memory copies: no global round trip per tile
+        at.pl = &si.pl;
         at.gj0 = si.gj0;
         at.n0 = si.n0;
         at.m0 = si.m0;
