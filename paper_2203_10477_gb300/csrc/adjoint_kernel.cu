@@ -697,7 +697,7 @@ cudaError_t adj_launch(int v, const void* params, int grid, cudaStream_t s)
 namespace {
 
 struct WsEntry {
-    int dtype, form, W, SA;
+    int dtype, form, W, SA, threads;
     const void* fn;
     size_t smem;
 };
@@ -706,7 +706,7 @@ template <typename Real, int FORM, int P, int NT, int SA>
 WsEntry make_ws()
 {
     constexpr int W = NT * P;
-    return WsEntry{sizeof(Real) == 8 ? kF64 : kF32, FORM, W, SA,
+    return WsEntry{sizeof(Real) == 8 ? kF64 : kF32, FORM, W, SA, NT + 32,
                    reinterpret_cast<const void*>(&adjoint_kernel_ws<Real, FORM, P, NT, SA>),
                    sizeof(Real) * ((8 + SA) * W + 4 * (NT / 32))};
 }
@@ -751,7 +751,7 @@ cudaError_t adj_ws_occupancy(int dtype, int form, int* blocks_per_sm)
     if (!e) return cudaErrorInvalidValue;
     cudaError_t st = adj_ws_prepare(dtype, form);
     if (st != cudaSuccess) return st;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, e->fn, 128 + 32, e->smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, e->fn, e->threads, e->smem);
 }
 
 cudaError_t adj_ws_launch(int dtype, int form, const void* params, int grid, cudaStream_t s)
@@ -759,7 +759,7 @@ cudaError_t adj_ws_launch(int dtype, int form, const void* params, int grid, cud
     const WsEntry* e = ws_find(dtype, form);
     if (!e) return cudaErrorInvalidValue;
     void* args[] = {const_cast<void*>(params)};
-    return cudaLaunchKernel(e->fn, dim3(grid), dim3(128 + 32), args, e->smem, s);
+    return cudaLaunchKernel(e->fn, dim3(grid), dim3(e->threads), args, e->smem, s);
 }
 
 cudaError_t adj_init_launch(int dtype, int form, void* l0, void* l1, const void* prob_l, int nprob, const void* wbar,
