@@ -85,6 +85,23 @@ def measured_traffic(dtype: str, variant: int, span: int):
     return None
 
 
+# Arithmetic instructions per update of each measured path (the pipe that bounds it):
+# forward span kernel: FP64 canonical 3 (add, 2 fma), FP32 increment 4 (2 sub, fma, add);
+# dL/dfA alone: the adjoint variables through the same span kernel;
+# dL/dfA and dL/da: checkpoint sweep (3 / 4) + adjoint kernel (recompute 3 / 4, Laplacian
+# 1 / 0 (the increment form's second difference is the Laplacian), pairing 1, adjoint step 3 / 4).
+ADJ_OPS = {"f64": {"g": 3, "full": 3 + 3 + 1 + 1 + 3}, "f32": {"g": 4, "full": 4 + 4 + 0 + 1 + 4}}
+
+
+def alu_roofline(dtype: str, value: float, ops: int) -> dict:
+    """ALU roofline of a path doing `ops` arithmetic instructions per update on the
+    FP64 pipe (2 / clock / SM) or the FP32 pipe (128 lanes / clock / SM) at 2070 MHz."""
+    lanes = 2 if dtype == "f64" else 128
+    peak = SM_COUNT * lanes * 2.07e9 / ops / 1e9
+    return {"bound": "alu", "unit": "GLUP/s", "peak": peak, "frac": value / peak,
+            "ops_per_update": ops, "pipe": "fp64" if dtype == "f64" else "fp32"}
+
+
 def alu_peaks(sm_mhz: float) -> dict:
     """Arithmetic-pipe-bound LUP rates of the span kernel's fast path.
 
@@ -421,7 +438,8 @@ def bench_batched(torch, rank, world, dist, dev):
     return {"workload": "4096 problems, nx U[2^10,2^18], a U[0.5,2], CFL 0.8, 4096 steps, overlap 32, FP32",
             "value": tot / t / 1e9, "unit": UNIT, "ms_per_run": 1e3 * t, "lups_per_run": tot,
             "variant": info["variant"], "span_steps": info["span_steps"], "mode": info["mode"],
-            "sharding": f"{world} rank(s), whole problems per rank"}
+            "sharding": f"{world} rank(s), whole problems per rank",
+            "roofline": alu_roofline("f32", tot / t / 1e9 / world, 4)}
 
 
 def bench_adjoint(torch, dev):
@@ -446,8 +464,12 @@ def bench_adjoint(torch, dev):
         ms_g = _time(torch, gonly, 2)
         plan.check()
         lups = (p.nx - 2) * p.T
-        res[name] = {"grad_fA_and_a": {"value": lups / (min(ms_full) / 1e3) / 1e9, "ms": min(ms_full)},
-                     "grad_fA_only": {"value": lups / (min(ms_g) / 1e3) / 1e9, "ms": min(ms_g)}}
+        v_full = lups / (min(ms_full) / 1e3) / 1e9
+        v_g = lups / (min(ms_g) / 1e3) / 1e9
+        res[name] = {"grad_fA_and_a": {"value": v_full, "ms": min(ms_full),
+                                       "roofline": alu_roofline(name, v_full, ADJ_OPS[name]["full"])},
+                     "grad_fA_only": {"value": v_g, "ms": min(ms_g),
+                                      "roofline": alu_roofline(name, v_g, ADJ_OPS[name]["g"])}}
     res["unit"] = UNIT
     res["workload"] = "c4: nx=2^20, a=1.3, CFL 0.9, 8192 steps, N=256, overlap 64, receiver j_r=4000"
     return res
@@ -469,8 +491,10 @@ def bench_large(torch, dev):
     lups = (p.nx - 2) * p.T
     info = plan.info()
     del out
-    return {"workload": "c5: nx=2^28 FP32, N=8192, overlap 64, 2^15 steps", "value": lups / (ms[0] / 1e3) / 1e9,
-            "unit": UNIT, "ms_per_run": ms[0], "variant": info["variant"], "span_steps": info["span_steps"]}
+    v = lups / (ms[0] / 1e3) / 1e9
+    return {"workload": "c5: nx=2^28 FP32, N=8192, overlap 64, 2^15 steps", "value": v,
+            "unit": UNIT, "ms_per_run": ms[0], "variant": info["variant"], "span_steps": info["span_steps"],
+            "roofline": alu_roofline("f32", v, 4)}
 
 
 def bench_c5_batch(torch, rank, world, dist, dev):
@@ -507,8 +531,10 @@ def bench_c5_batch(torch, rank, world, dist, dev):
     del out, wbar
     return {"workload": "c5: 512 uneven problems, nx U[2^12,2^20], a U[0.5,2], CFL 0.9, overlap 64, 2^15 steps, FP32",
             "unit": UNIT, "lups_per_run": tot,
-            "forward": {"value": tot / t_f / 1e9, "ms_per_run": t_f * 1e3},
-            "adjoint_grad_fA": {"value": tot / t_a / 1e9, "ms_per_run": t_a * 1e3},
+            "forward": {"value": tot / t_f / 1e9, "ms_per_run": t_f * 1e3,
+                        "roofline": alu_roofline("f32", tot / t_f / 1e9, 4)},
+            "adjoint_grad_fA": {"value": tot / t_a / 1e9, "ms_per_run": t_a * 1e3,
+                                "roofline": alu_roofline("f32", tot / t_a / 1e9, 4)},
             "variant": info["variant"], "span_steps": info["span_steps"], "mode": info["mode"],
             "sharding": f"{world} rank(s), whole problems per rank"}
 
