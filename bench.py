@@ -453,6 +453,7 @@ def bench_adjoint(torch, dev):
     w = torch.as_tensor(inputs.lowpass_noise(p.T, seed=4), device=dev)
     for name, dtype in (("f64", rswr.F64), ("f32", rswr.F32)):
         plan = rswr.Plan.from_problem(p, dtype=dtype, device=dev)
+        plan.autotune(64)  # variant, mode and span of the sweeps through the span kernel
         td = torch.float64 if dtype == rswr.F64 else torch.float32
         fA = torch.as_tensor(p.fA, device=dev).to(td)
         wt = w.to(td)
@@ -470,6 +471,9 @@ def bench_adjoint(torch, dev):
                                        "roofline": alu_roofline(name, v_full, ADJ_OPS[name]["full"])},
                      "grad_fA_only": {"value": v_g, "ms": min(ms_g),
                                       "roofline": alu_roofline(name, v_g, ADJ_OPS[name]["g"])}}
+        res[name]["variant"] = plan.info()["variant"]
+        res[name]["mode"] = plan.info()["mode"]
+        res[name]["span_steps"] = plan.info()["span_steps"]
     res["unit"] = UNIT
     res["workload"] = "c4: nx=2^20, a=1.3, CFL 0.9, 8192 steps, N=256, overlap 64, receiver j_r=4000"
     return res
