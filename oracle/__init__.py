@@ -74,11 +74,11 @@ def _declare(L):
     for suf, R in (("f64", _dbl), ("f32", _flt)):
         f = getattr(L, f"oracle_leapfrog_{suf}")
         f.argtypes = [ctypes.c_int, _i64, _i64, R, R, _vp, _vp, _vp, _vp, _vp, _vp,
-                      _i64, _vp, _vp, _i64, _vp, R, _vp, _i64, _vp]
+                      _i64, _vp, _vp, _i64, _vp, R, _vp, _i64, _vp, _vp]
         f.restype = ctypes.c_int
         g = getattr(L, f"oracle_rswr_mask_{suf}")
         g.argtypes = [ctypes.c_int, _i64, _i64, R, R, _vp, _vp, _vp, _vp, _i64, _i64, _i64,
-                      _vp, _vp, R, _vp]
+                      _vp, _vp, R, _vp, _i64, _vp, _vp]
         g.restype = ctypes.c_int
     L.oracle_rswr_paper.argtypes = [ctypes.c_int, _i64, _i64, _dbl, _dbl, _dbl, _dbl, _vp, _vp,
                                     _i64, _i64, _i64, _dbl, _vp, _vp, _vp, _vp]
@@ -131,14 +131,31 @@ def _cf(cf: Coeffs, prec: str):
     return float(cf.c2f), float(cf.kf), float(cf.inv2dxf)
 
 
+def _sources(src_j, src, T, dt_):
+    """(count, points, samples[count, T+1]) from one point (int, src 1-D) or a list."""
+    if src is None:
+        return 0, None, None
+    src = np.asarray(src, dtype=dt_)
+    if np.ndim(src_j) == 0:
+        j = np.array([int(src_j)], dtype=np.int64)
+        src = src.reshape(1, -1)
+    else:
+        j = np.ascontiguousarray(src_j, dtype=np.int64)
+    src = np.ascontiguousarray(src.reshape(len(j), -1), dtype=dt_)
+    assert src.shape == (len(j), T + 1)
+    return len(j), j, src
+
+
 def leapfrog(nx, T, a, dt, fA, fB, *, form=CANONICAL, prec="f64", q0=None, q1=None,
              rec_j=(), flux_j=(), xa=0.0, xb=1.0, nx_run=None, src_j=-1, src=None):
     """Monolithic leapfrog.  Returns dict(u=final q0, w=final q1, rec, flux, coeffs).
 
     The coefficients come from the grid (xa, xb, nx); ``nx_run`` < nx runs the
     same grid truncated to its first nx_run points (see ``causal_extent``).
-    ``src`` (T+1 values) adds src[n] at the interior point ``src_j`` when level
-    n is formed (the source term of the discrete adjoint)."""
+    Interior point sources (the paper's pulse sources, Sec. 4; one of them is
+    also the source term of the discrete adjoint): ``src_j`` one point or a list
+    of K points, ``src`` T+1 samples or a (K, T+1) array; sample n is added at
+    the point when level n is formed, in list order."""
     dt_, suf = _prec(prec)
     cf = coeffs(xa, xb, a, nx, dt)
     nx = nx if nx_run is None else int(nx_run)
@@ -154,20 +171,19 @@ def leapfrog(nx, T, a, dt, fA, fB, *, form=CANONICAL, prec="f64", q0=None, q1=No
     fj = np.ascontiguousarray(flux_j, dtype=np.int64)
     rec = np.empty((len(rj), T + 1), dt_)
     flux = np.empty((len(fj), T + 1), dt_)
-    src = _arr(src, dt_)
-    if src is not None:
-        assert src.shape == (T + 1,)
+    ns, sj, sv = _sources(src_j, src, T, dt_)
     rc = getattr(lib(), f"oracle_leapfrog_{suf}")(form, nx, T, c2, k, _ptr(fA), _ptr(fB), _ptr(q0), _ptr(q1),
                                                   _ptr(out0), _ptr(out1), len(rj), _ptr(rj), _ptr(rec),
-                                                  len(fj), _ptr(fj), inv2dx, _ptr(flux), int(src_j), _ptr(src))
+                                                  len(fj), _ptr(fj), inv2dx, _ptr(flux), ns, _ptr(sj), _ptr(sv))
     if rc:
         raise RuntimeError(f"oracle_leapfrog failed ({rc})")
     return {"u": out0, "w": out1, "rec": rec, "flux": flux, "coeffs": cf}
 
 
 def rswr_mask(nx, T, a, dt, fA, fB, N, ov, *, S=None, form=CANONICAL, prec="f64", q0=None, q1=None,
-              xa=0.0, xb=1.0, traces=True):
-    """Serial RSWR (index-mask select).  Returns dict(u, w, traces[(N-1),2,T+1])."""
+              xa=0.0, xb=1.0, traces=True, src_j=(), src=None):
+    """Serial RSWR (index-mask select).  Returns dict(u, w, traces[(N-1),2,T+1]).
+    Point sources as in ``leapfrog``, applied inside every window that holds them."""
     dt_, suf = _prec(prec)
     cf = coeffs(xa, xb, a, nx, dt)
     c2, k, inv2dx = _cf(cf, prec)
@@ -180,9 +196,10 @@ def rswr_mask(nx, T, a, dt, fA, fB, N, ov, *, S=None, form=CANONICAL, prec="f64"
     out0 = np.empty(nx, dt_)
     out1 = np.empty(nx, dt_)
     tr = np.zeros((max(N - 1, 0), 2, T + 1), dt_) if traces else None
+    ns, sj, sv = _sources(src_j, src, T, dt_)
     rc = getattr(lib(), f"oracle_rswr_mask_{suf}")(form, nx, T, c2, k, _ptr(fA), _ptr(fB), _ptr(q0), _ptr(q1),
                                                    N, ov, S, _ptr(out0), _ptr(out1), inv2dx,
-                                                   _ptr(tr) if (traces and N > 1) else None)
+                                                   _ptr(tr) if (traces and N > 1) else None, ns, _ptr(sj), _ptr(sv))
     if rc:
         raise RuntimeError(f"oracle_rswr_mask failed ({rc})")
     return {"u": out0, "w": out1, "traces": tr, "coeffs": cf}

@@ -65,6 +65,28 @@ static void NAME(init_state)(int form, int64_t nx, const REAL* fA, const REAL* f
     w[nx - 1] = (form == 0) ? u[nx - 1] : (REAL)0;
 }
 
+/* Interior point sources entering level n+1 (the paper's pulse sources,
+ * Sec. 4; with one source, also the source term of the discrete adjoint):
+ * source q adds src[q*(T+1) + n+1] at point src_j[q] when level n+1 is formed,
+ * to the new value (form 0) or to the new increment before it is applied
+ * (form 1), in the order q = 0, 1, ...  Only points in [lo, hi] that are not a
+ * Dirichlet node are touched; u_old is level n (form 1 recomputes u = u_old + v). */
+static void NAME(add_sources)(int form, int64_t nx, int64_t T, int64_t n, int64_t nsrc, const int64_t* src_j,
+                              const REAL* src, int64_t lo, int64_t hi, const REAL* u_old, REAL* un, REAL* wn)
+{
+    for (int64_t q = 0; q < nsrc; ++q) {
+        int64_t j = src_j[q];
+        if (j <= 0 || j >= nx - 1 || j < lo || j > hi) continue;
+        REAL s = src[q * (T + 1) + n + 1];
+        if (form == 0) {
+            un[j] = un[j] + s;
+        } else {
+            wn[j] = wn[j] + s;
+            un[j] = u_old[j] + wn[j];
+        }
+    }
+}
+
 /* Value and flux probes of one level: rec[r*(T+1)+n] = u_j, flux = (u_{j+1}-u_{j-1})*inv2dx. */
 static void NAME(record)(int64_t n, int64_t T, const REAL* u, int64_t nrec, const int64_t* rec_j,
                          REAL* rec, int64_t nflux, const int64_t* flux_j, REAL inv2dx, REAL* flux)
@@ -86,7 +108,7 @@ int NAME(oracle_leapfrog)(int form, int64_t nx, int64_t T, REAL c2, REAL k,
                           REAL* out0, REAL* out1,
                           int64_t nrec, const int64_t* rec_j, REAL* rec,
                           int64_t nflux, const int64_t* flux_j, REAL inv2dx, REAL* flux,
-                          int64_t src_j, const REAL* src)
+                          int64_t nsrc, const int64_t* src_j, const REAL* src)
 {
     if (nx < 3 || T < 0 || (form != 0 && form != 1)) return 1;
     REAL* u = (REAL*)malloc(sizeof(REAL) * nx);
@@ -99,17 +121,7 @@ int NAME(oracle_leapfrog)(int form, int64_t nx, int64_t T, REAL c2, REAL k,
     for (int64_t n = 0; n < T; ++n) {
         for (int64_t j = 1; j < nx - 1; ++j)
             NAME(point_update)(form, c2, k, u[j - 1], u[j], u[j + 1], w[j], &un[j], &wn[j]);
-        /* optional point source entering level n+1 at src_j (the source term of the
-         * discrete adjoint): added to the new value (form 0) or to the new
-         * increment before it is applied (form 1) */
-        if (src && src_j > 0 && src_j < nx - 1) {
-            if (form == 0) {
-                un[src_j] = un[src_j] + src[n + 1];
-            } else {
-                wn[src_j] = wn[src_j] + src[n + 1];
-                un[src_j] = u[src_j] + wn[src_j];
-            }
-        }
+        if (src && nsrc > 0) NAME(add_sources)(form, nx, T, n, nsrc, src_j, src, 1, nx - 2, u, un, wn);
         un[0] = fA[n + 1];
         wn[0] = NAME(dirichlet_w)(form, fA[n], fA[n + 1]);
         un[nx - 1] = fB[n + 1];
@@ -154,7 +166,7 @@ int NAME(oracle_leapfrog)(int form, int64_t nx, int64_t T, REAL c2, REAL k,
 int NAME(oracle_rswr_mask)(int form, int64_t nx, int64_t T, REAL c2, REAL k,
                            const REAL* fA, const REAL* fB, const REAL* q0, const REAL* q1,
                            int64_t N, int64_t ov, int64_t S, REAL* out0, REAL* out1,
-                           REAL inv2dx, REAL* traces)
+                           REAL inv2dx, REAL* traces, int64_t nsrc, const int64_t* src_j, const REAL* src)
 {
     if (nx < 3 || T < 0 || N < 1 || ov < 2 || S < 1 || (form != 0 && form != 1)) return 1;
     int64_t el = (ov + 1) / 2, er = ov / 2;
@@ -207,6 +219,8 @@ int NAME(oracle_rswr_mask)(int form, int64_t nx, int64_t T, REAL c2, REAL k,
                         NAME(point_update)(form, c2, k, uL, pu[j], uR, pw[j], &qu[j], &qw[j]);
                     }
                 }
+                /* the sources inside the window, halo included (Sec. 4 pulse sources) */
+                if (src && nsrc > 0) NAME(add_sources)(form, nx, T, n, nsrc, src_j, src, L, R, pu, qu, qw);
                 for (int64_t j = L; j <= R; ++j) { pu[j] = qu[j]; pw[j] = qw[j]; }
                 /* boundary output waveforms of this window (Sec. 2.2 definitions) */
                 if (traces) {

@@ -12,9 +12,18 @@ from __future__ import annotations
 from fractions import Fraction
 
 
-def leapfrog(nx, T, c2, k, fA, fB, u0=None, up=None):
+def _sources(new, n, nx, sources, lo=1, hi=None):
+    """Point sources (j, samples): samples[n + 1] joins level n + 1 at interior point j."""
+    hi = nx - 2 if hi is None else hi
+    for j, smp in sources:
+        if 0 < j < nx - 1 and lo <= j <= hi:
+            new[j] += Fraction(smp[n + 1])
+
+
+def leapfrog(nx, T, c2, k, fA, fB, u0=None, up=None, sources=()):
     """u^{n+1}_j = c2 (u^n_{j-1} + u^n_{j+1}) + k u^n_j - u^{n-1}_j on interior j,
-    Dirichlet fA/fB; zero initial data with u^{-1} = u^0 unless given.
+    Dirichlet fA/fB; zero initial data with u^{-1} = u^0 unless given; point
+    sources [(j, samples)] add samples[n+1] at j when level n+1 is formed.
     Returns the list of all levels u^0..u^T."""
     u = [Fraction(0)] * nx if u0 is None else [Fraction(x) for x in u0]
     u[0], u[-1] = Fraction(fA[0]), Fraction(fB[0])
@@ -24,16 +33,18 @@ def leapfrog(nx, T, c2, k, fA, fB, u0=None, up=None):
         new = [Fraction(0)] * nx
         for j in range(1, nx - 1):
             new[j] = c2 * (u[j - 1] + u[j + 1]) + k * u[j] - prev[j]
+        _sources(new, n, nx, sources)
         new[0], new[-1] = Fraction(fA[n + 1]), Fraction(fB[n + 1])
         prev, u = u, new
         levels.append(list(u))
     return levels
 
 
-def rswr_mask(nx, T, c2, k, fA, fB, N, ov, S, u0=None, up=None):
+def rswr_mask(nx, T, c2, k, fA, fB, N, ov, S, u0=None, up=None, sources=()):
     """Serial RSWR with zero-flux (mirror) predictions and core write-back.
     Windows extend ceil(ov/2) left and floor(ov/2) right of the cores
-    b_i = floor(i nx / N).  Returns the final level pair (u^T, u^{T-1})."""
+    b_i = floor(i nx / N); each window applies the point sources it contains.
+    Returns the final level pair (u^T, u^{T-1})."""
     el, er = (ov + 1) // 2, ov // 2
     u = [Fraction(0)] * nx if u0 is None else [Fraction(x) for x in u0]
     u[0], u[-1] = Fraction(fA[0]), Fraction(fB[0])
@@ -60,6 +71,9 @@ def rswr_mask(nx, T, c2, k, fA, fB, N, ov, S, u0=None, up=None):
                         left = cu[j + 1] if j == L else cu[j - 1]
                         right = cu[j - 1] if j == R else cu[j + 1]
                         new[j] = c2 * (left + right) + k * cu[j] - cp[j]
+                for j, smp in sources:
+                    if 0 < j < nx - 1 and L <= j <= R:
+                        new[j] += Fraction(smp[n + 1])
                 cp, cu = cu, new
             for j in range(b0, b1):
                 nu[j] = cu[j]

@@ -60,6 +60,15 @@ MUTANTS = {
                                         "if (j == R) uR = gR ? pu[j - 1] - 2.0 * dx * gR[s] : pu[j - 1];"),
     "paper-literal: combination": ("rswr_oracle.c", "int64_t from = (i == 0) ? L : win_right(i - 1, nx, N, er) + 1;",
                                    "int64_t from = (i == 0) ? L : win_right(i - 1, nx, N, er) + 2;"),
+    "source: time level": ("leapfrog_body.h", "REAL s = src[q * (T + 1) + n + 1];", "REAL s = src[q * (T + 1) + n];"),
+    "source: sign": ("leapfrog_body.h", "            un[j] = un[j] + s;", "            un[j] = un[j] - s;"),
+    "source: increment not applied": ("leapfrog_body.h", "            un[j] = u_old[j] + wn[j];",
+                                      "            un[j] = u_old[j];"),
+    # (skipping only the two window end points cannot be caught: they are the
+    # guessed input boundaries, whose values never reach the kept core)
+    "source: only in the window's core": ("leapfrog_body.h",
+                                          "if (src && nsrc > 0) NAME(add_sources)(form, nx, T, n, nsrc, src_j, src, L, R, pu, qu, qw);",
+                                          "if (src && nsrc > 0) NAME(add_sources)(form, nx, T, n, nsrc, src_j, src, b0, b1 - 1, pu, qu, qw);"),
 }
 
 
@@ -191,7 +200,37 @@ def chk_adjoint():
     return bool(ok)
 
 
-CHECKS = {"dalembert": chk_dalembert, "mode": chk_mode, "rational-canonical": lambda: chk_rational(0),
+def chk_sources():
+    """Point sources at Courant number 1 form lattice light cones (closed form),
+    in both forms; serial RSWR with sources in halos equals the monolithic solve."""
+    nx, T = 201, 40
+    dt = 1.0 / (nx - 1)
+    z = np.zeros(T + 1)
+    r = inputs.rng(6)
+    pts = [60, 100, 100, 141]  # the cones stay clear of both Dirichlet nodes
+    smp = np.zeros((len(pts), T + 1))
+    smp[:, 1:] = r.integers(-3, 4, size=(len(pts), T))
+    ref = np.zeros(nx)
+    for j0, sm in zip(pts, smp):
+        for m in range(1, T + 1):
+            for d in range(-(T - m), T - m + 1, 2):
+                ref[j0 + d] += sm[m]
+    ok = True
+    for form in (0, 1):
+        ok &= np.array_equal(oracle.leapfrog(nx, T, 1.0, dt, z, z, form=form, src_j=pts, src=smp)["u"], ref)
+    nx, N, ov, T = 301, 4, 12, 90
+    dt = 0.7 / (nx - 1)
+    z = np.zeros(T + 1)
+    pts = [70, 74, 76, 150]  # in the first interface's overlap and halos
+    smp = np.stack([inputs.gaussian_pulse(T, dt, sigma_steps=8) * (i + 1) for i in range(len(pts))])
+    for form in (0, 1):
+        m = oracle.leapfrog(nx, T, 1.0, dt, z, z, form=form, src_j=pts, src=smp)
+        s = oracle.rswr_mask(nx, T, 1.0, dt, z, z, N, ov, form=form, src_j=pts, src=smp)
+        ok &= np.array_equal(m["u"], s["u"]) and np.array_equal(m["w"], s["w"])
+    return bool(ok)
+
+
+CHECKS = {"sources": chk_sources, "dalembert": chk_dalembert, "mode": chk_mode, "rational-canonical": lambda: chk_rational(0),
           "rational-increment": lambda: chk_rational(1), "energy": chk_energy, "rswr": chk_rswr,
           "paper": chk_paper, "adjoint": chk_adjoint}
 

@@ -425,3 +425,93 @@ def test_source_driven_leapfrog_is_the_adjoint_sweep(oracle_mod):
     dg = np.array([c2 * lam["rec"][0][T - n] for n in range(T + 1)])
     assert np.array_equal(dg[:T], adj["dg"][:T])
     assert dg[T] == 0.0 and adj["dg"][T] == 0.0
+
+
+# ----------------------------------------------------------------------------
+# interior point sources (the paper's pulse sources, Sec. 4)
+# ----------------------------------------------------------------------------
+
+def lattice_light_cone(nx, T, sources):
+    """Closed form of the leapfrog at Courant number 1 far from the boundaries:
+    a unit impulse joining level m at point j0 is, at level n >= m, 1 at every j
+    with |j - j0| <= n - m and j - j0 = n - m (mod 2), 0 elsewhere (the lattice
+    d'Alembert solution: it spreads one cell per step in a checkerboard).  A
+    source with samples s^m superposes s^m times that pattern."""
+    u = np.zeros(nx)
+    for j0, smp in sources:
+        for m in range(1, T + 1):
+            if smp[m] == 0:
+                continue
+            t = T - m
+            for d in range(-t, t + 1, 2):
+                u[j0 + d] += smp[m]
+    return u
+
+
+@pytest.mark.parametrize("form", [CAN, INC])
+def test_sources_at_cfl1_form_lattice_light_cones(oracle_mod, form):
+    nx, T = 301, 80
+    dt = 1.0 / (nx - 1)  # Courant number 1
+    r = np.random.default_rng(5)
+    sources = []
+    for j0 in (100, 150, 150, 201):  # two sources share a point
+        smp = np.zeros(T + 1)
+        smp[1:] = r.integers(-3, 4, size=T)
+        sources.append((j0, smp))
+    z = np.zeros(T + 1)
+    out = oracle_mod.leapfrog(nx, T, 1.0, dt, z, z, form=form, src_j=[j for j, _ in sources],
+                              src=np.stack([s for _, s in sources]))
+    assert np.array_equal(out["u"], lattice_light_cone(nx, T, sources))
+
+
+@pytest.mark.parametrize("N,ov", [(2, 4), (3, 6), (4, 5)])
+def test_rswr_with_sources_exact_in_rationals_and_tight(N, ov):
+    """With point sources inside windows, in halos and on core boundaries the
+    combined RSWR state still equals the monolithic state exactly for
+    S <= floor(ov/2) (the sources are local; the discrete domain of dependence
+    is unchanged), and S = floor(ov/2) + 1 still breaks it."""
+    nx, T, fA, fB = _tiny_case(40 + N + ov, nx=31, T=29)
+    c2 = Fraction(9, 25)
+    k = 2 - 2 * c2
+    r = np.random.default_rng(N * 10 + ov)
+    b1 = nx // N
+    pts = sorted({2, b1 - 1, b1, b1 + 1, nx - 3})
+    sources = [(j, np.concatenate([[0.0], np.round(r.standard_normal(T) * 4) / 4])) for j in pts]
+    mono = rr.leapfrog(nx, T, c2, k, fA, fB, sources=sources)
+    u, prev = rr.rswr_mask(nx, T, c2, k, fA, fB, N, ov, ov // 2, sources=sources)
+    assert u == mono[-1] and prev == mono[-2]
+    u_bad, _ = rr.rswr_mask(nx, T, c2, k, fA, fB, N, ov, ov // 2 + 1, sources=sources)
+    assert u_bad != mono[-1]
+
+
+@pytest.mark.parametrize("form", [CAN, INC])
+def test_oracle_sources_within_rounding_of_exact_rationals(oracle_mod, form):
+    nx, T, fA, fB = _tiny_case(17, nx=41, T=37)
+    dt = 0.6 / (nx - 1)
+    cf = oracle_mod.coeffs(0.0, 1.0, 1.0, nx, dt)
+    c2 = Fraction(cf.c2)
+    k = Fraction(cf.k) if form == CAN else 2 - 2 * c2
+    r = np.random.default_rng(3)
+    pts = [5, 20, 20, 33]
+    smp = np.zeros((len(pts), T + 1))
+    smp[:, 1:] = np.round(r.standard_normal((len(pts), T)) * 8) / 8
+    levels = rr.leapfrog(nx, T, c2, k, fA, fB, sources=list(zip(pts, smp)))
+    exact = np.array([float(v) for v in levels[-1]])
+    out = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, fB, form=form, src_j=pts, src=smp)
+    assert np.abs(out["u"] - exact).max() <= 1e-12 * max(1.0, np.abs(exact).max())
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("form", [CAN, INC])
+def test_rswr_mask_with_sources_equals_monolithic_bitwise(oracle_mod, prec, form):
+    nx, N, ov, T = 1001, 10, 16, 300
+    dt = 0.8 / (nx - 1)
+    fA = inputs.ramped_sine(T, dt, freq=9.0)
+    z = np.zeros(T + 1)
+    pts = [50, 99, 100, 107, 450, 450, 951, 998]  # inside cores, on core edges, in halos, shared, near j = nx-1
+    src = np.stack([inputs.gaussian_pulse(T, dt, sigma_steps=10 + 3 * i) * (1 + i) for i in range(len(pts))])
+    mono = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, z, form=form, prec=prec, src_j=pts, src=src)
+    rs = oracle_mod.rswr_mask(nx, T, 1.0, dt, fA, z, N, ov, form=form, prec=prec, src_j=pts, src=src)
+    assert np.abs(mono["u"]).max() > 0.1
+    assert np.array_equal(rs["u"], mono["u"])
+    assert np.array_equal(rs["w"], mono["w"])
