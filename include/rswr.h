@@ -145,6 +145,24 @@ rswr_status rswr_plan_set_wait_limit(rswr_plan_t plan, double seconds);
  * spans < 0. */
 rswr_status rswr_plan_set_checkpoint_spacing(rswr_plan_t plan, int64_t spans);
 
+/* Point sources (the pulse sources of the paper's Sec. 4 experiments), used
+ * by rswr_run, rswr_run_host and rswr_mono until replaced.  Source q sits at
+ * grid point j[q] (host array, 0 <= j[q] < nx) and has the samples
+ * samples[q * pitch + n], n = 0..T (DEVICE memory in the plan's dtype, owned
+ * by the caller and kept alive while the set is active; pitch >= T+1 of
+ * every run, else that run fails with RSWR_EINVAL).  When level n+1 is formed
+ * (n = 0..T-1) the sample of level n+1 is added at j[q]: to u^{n+1} in the
+ * canonical form; to the increment v^{n+1}, after which u^{n+1} = u^n +
+ * v^{n+1}, in the increment form.  Several sources at one point apply in list
+ * order; a source on a Dirichlet node (j = 0 or nx-1) never applies.  Every
+ * RSWR window containing j (halo included) applies the source, so rswr_run
+ * stays bit-identical to rswr_mono.  nsrc = 0 clears the set.  rswr_adjoint
+ * and rswr_run_paper return RSWR_ENOTSUP while a set is active.
+ * Errors: EINVAL (point outside the grid, pitch < 1, NULL arrays, samples not
+ * aligned to the element size). */
+rswr_status rswr_plan_set_sources(rswr_plan_t plan, int64_t nsrc, const int64_t* j, const void* samples,
+                                  int64_t pitch);
+
 /* Failure-injection hook for tests: in persistent mode, CTA tile `tile` does
  * not publish completion of span `span`, so its neighbours' bounded waits
  * expire and the run reports RSWR_ETIMEOUT.  tile = -1 disables. */
@@ -276,6 +294,10 @@ rswr_status rswr_batch_set_variant(rswr_batch_t batch, int32_t variant);
 rswr_status rswr_batch_set_wait_limit(rswr_batch_t batch, double seconds);
 rswr_status rswr_batch_set_checkpoint_spacing(rswr_batch_t batch, int64_t spans);
 rswr_status rswr_batch_set_kernel_events(rswr_batch_t batch, void* start, void* stop);
+/* rswr_plan_set_sources for a batch: source q belongs to problem problem[q]
+ * (host array) and sits at its grid point j[q]; used by rswr_batch_run. */
+rswr_status rswr_batch_set_sources(rswr_batch_t batch, int64_t nsrc, const int32_t* problem, const int64_t* j,
+                                   const void* samples, int64_t pitch);
 rswr_status rswr_batch_set_graph(rswr_batch_t batch, int32_t enable);
 /* As rswr_plan_autotune, over the batch's own problems. */
 rswr_status rswr_batch_autotune(rswr_batch_t batch, int64_t probe_steps, int32_t* variant, void* stream);

@@ -54,6 +54,8 @@ __device__ __forceinline__ void probe_one(const ProbeDev<Real>& pr, const Real* 
     if (n <= pr.nmax) pr.out[n * pr.stride] = val;
 }
 
+static_assert(kMonoBlockPoints == 256 * 4, "block CSR of the sources assumes 256 threads x 4 points");
+
 template <typename Real, int FORM>
 __global__ void __launch_bounds__(256) mono_step_kernel(const __grid_constant__ MonoParams<Real> p)
 {
@@ -98,6 +100,26 @@ __global__ void __launch_bounds__(256) mono_step_kernel(const __grid_constant__ 
             } else if (j > p.nx - 1) {
                 out_u[i] = Real(0);
                 if constexpr (FORM == kIncrement) out_w[i] = Real(0);
+            }
+        }
+    }
+    // user point sources of this block's points, in the caller's order per point
+    if (p.blk_src) {
+        const int q1 = p.blk_src[blockIdx.x + 1];
+        for (int q = p.blk_src[blockIdx.x]; q < q1; ++q) {
+            const SrcDev<Real> sd = p.srcs[q];
+            const int64_t r = sd.j - j0;
+            if (r < 0 || r >= 4) continue;
+            const Real sv = sd.samples[p.n + 1];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (i != r) continue;
+                if constexpr (FORM == kCanonical) {
+                    out_u[i] = radd(out_u[i], sv);
+                } else {
+                    out_w[i] = radd(out_w[i], sv);
+                    out_u[i] = radd(u[i], out_w[i]);
+                }
             }
         }
     }

@@ -123,6 +123,17 @@ struct Engine {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<int64_t> graph_key;
+    // user point sources (rswr_plan_set_sources / rswr_batch_set_sources):
+    // problem, point and the sample row of each, in the caller's order
+    struct UserSrc {
+        int64_t p, j, row;
+    };
+    std::vector<UserSrc> usrc;
+    const void* usrc_samples = nullptr;  // device, row r at usrc_samples + r * usrc_pitch elements
+    int64_t usrc_pitch = 0;
+    void* d_srcs = nullptr;  // the device source tables of the last run
+    size_t srcs_cap = 0;     // bytes
+    bool srcs_live = false;  // the last span run's tiles hold sources (selects the kernels compiled for them)
 
     size_t esize() const { return dtype == kF64 ? 8 : 4; }
 };
@@ -139,6 +150,7 @@ void free_engine(Engine* e)
     cudaFree(e->d_problems);
     cudaFree(e->d_tiles);
     cudaFree(e->d_probes);
+    cudaFree(e->d_srcs);
     cudaFree(e->d_offsets);
     cudaFree(e->d_ticket);
     cudaFree(e->d_done);
@@ -395,6 +407,7 @@ struct RunReq {
     int64_t src_pitch = 0;
     int64_t src_stride = 1;
     bool mono = false;
+    bool user_src = false;  // apply the engine's user point sources
 };
 
 template <typename Real>
@@ -426,7 +439,7 @@ rswr_status upload_problems(Engine* e, const RunReq& r, cudaStream_t s)
 }
 
 template <typename Real>
-rswr_status upload_probes(Engine* e, const RunReq& r, int* nprobe, cudaStream_t s)
+rswr_status upload_probes(Engine* e, const RunReq& r, int* nprobe, bool* tiles_dirty, cudaStream_t s)
 {
     std::vector<ProbeDev<Real>> h;
     h.reserve(r.probes.size());
@@ -460,9 +473,7 @@ rswr_status upload_probes(Engine* e, const RunReq& r, int* nprobe, cudaStream_t 
         td.probe_begin = (int32_t)q;
         td.probe_end = (int32_t)q2;
     }
-    if (changed)
-        RSWR_CUDA(cudaMemcpyAsync(e->d_tiles, e->h_tiles.data(), sizeof(TileDev) * e->h_tiles.size(),
-                                  cudaMemcpyHostToDevice, s));
+    *tiles_dirty |= changed;
     if (!h.empty()) {
         if (h.size() > e->probes_cap) {
             RSWR_CUDA(cudaStreamSynchronize(s));
@@ -477,6 +488,86 @@ rswr_status upload_probes(Engine* e, const RunReq& r, int* nprobe, cudaStream_t 
     return RSWR_OK;
 }
 
+int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Device tables of the user point sources of a run (one allocation):
+//   span runs: SrcDev entries grouped by tile -- every source whose point lies
+//     in the tile's window [t core - H, t core - H + W), in the caller's
+//     order -- with the ranges in TileDev::src_begin/src_end;
+//   monolithic runs: SrcDev entries sorted by point (stable), then the int32
+//     CSR of the step kernel's blocks (kMonoBlockPoints points each).
+// Sources at the Dirichlet nodes never apply (the boundary data wins).
+template <typename Real>
+rswr_status upload_sources(Engine* e, const RunReq& r, bool* tiles_dirty, int64_t* mono_blk_off, cudaStream_t s)
+{
+    *mono_blk_off = -1;
+    e->srcs_live = false;
+    std::vector<std::pair<int64_t, SrcDev<Real>>> ent;  // (sort key, entry)
+    const bool use = r.user_src && !e->usrc.empty();
+    if (use) {
+        if (e->usrc_pitch < r.T + 1) return fail(RSWR_EINVAL, "source samples hold fewer than T+1 levels");
+        for (const Engine::UserSrc& q : e->usrc) {
+            const ProbHost& ph = e->probs[q.p];
+            if (q.j <= 0 || q.j >= ph.nx - 1) continue;
+            const SrcDev<Real> d{q.j, static_cast<const Real*>(e->usrc_samples) + q.row * e->usrc_pitch};
+            if (r.mono) {
+                ent.push_back({q.j, d});
+                continue;
+            }
+            const int64_t t_lo = std::max<int64_t>(0, floor_div(q.j + e->H - e->W, e->core) + 1);
+            const int64_t t_hi = std::min<int64_t>(ph.ntiles - 1, floor_div(q.j + e->H, e->core));
+            for (int64_t t = t_lo; t <= t_hi; ++t) ent.push_back({ph.tile0 + t, d});
+        }
+        std::stable_sort(ent.begin(), ent.end(),
+                         [](const std::pair<int64_t, SrcDev<Real>>& a, const std::pair<int64_t, SrcDev<Real>>& b) {
+                             return a.first < b.first;
+                         });
+    }
+    // tile ranges (empty for monolithic runs and runs without sources)
+    size_t q = 0;
+    for (size_t t = 0; t < e->h_tiles.size(); ++t) {
+        TileDev& td = e->h_tiles[t];
+        size_t q2 = q;
+        if (!r.mono)
+            while (q2 < ent.size() && ent[q2].first == (int64_t)t) ++q2;
+        if (td.src_begin != (int32_t)q || td.src_end != (int32_t)q2) *tiles_dirty = true;
+        td.src_begin = (int32_t)q;
+        td.src_end = (int32_t)q2;
+        q = q2;
+    }
+    if (ent.empty()) return RSWR_OK;
+    std::vector<SrcDev<Real>> tab;
+    tab.reserve(ent.size());
+    for (const auto& x : ent) tab.push_back(x.second);
+    std::vector<int32_t> blk;
+    if (r.mono) {
+        const int64_t nblk = (e->probs[0].nx + kMonoBlockPoints - 1) / kMonoBlockPoints;
+        blk.resize(nblk + 1);
+        size_t i = 0;
+        for (int64_t b = 0; b <= nblk; ++b) {
+            while (i < ent.size() && ent[i].first < b * kMonoBlockPoints) ++i;
+            blk[b] = (int32_t)i;
+        }
+    }
+    const size_t tab_bytes = sizeof(SrcDev<Real>) * tab.size();
+    const size_t need = tab_bytes + sizeof(int32_t) * blk.size();
+    if (need > e->srcs_cap) {
+        RSWR_CUDA(cudaStreamSynchronize(s));
+        cudaFree(e->d_srcs);
+        e->d_srcs = nullptr;
+        e->srcs_cap = 0;
+        if (cudaMalloc(&e->d_srcs, need) != cudaSuccess) return fail(RSWR_ENOMEM, "source table");
+        e->srcs_cap = need;
+    }
+    std::vector<unsigned char> host(need);
+    std::memcpy(host.data(), tab.data(), tab_bytes);
+    if (!blk.empty()) std::memcpy(host.data() + tab_bytes, blk.data(), sizeof(int32_t) * blk.size());
+    RSWR_CUDA(cudaMemcpyAsync(e->d_srcs, host.data(), need, cudaMemcpyHostToDevice, s));
+    if (r.mono) *mono_blk_off = (int64_t)tab_bytes;
+    else e->srcs_live = true;
+    return RSWR_OK;
+}
+
 template <typename Real>
 SpanParams<Real> span_params(Engine* e, int64_t T, int nspans)
 {
@@ -484,6 +575,7 @@ SpanParams<Real> span_params(Engine* e, int64_t T, int nspans)
     prm.problems = static_cast<const ProblemDev<Real>*>(e->d_problems);
     prm.tiles = static_cast<const TileDev*>(e->d_tiles);
     prm.probes = static_cast<const ProbeDev<Real>*>(e->d_probes);
+    prm.srcs = e->srcs_live ? static_cast<const SrcDev<Real>*>(e->d_srcs) : nullptr;
     for (int b = 0; b < 2; ++b) {
         prm.q0[b] = static_cast<Real*>(e->q0[b]);
         prm.q1[b] = static_cast<Real*>(e->q1[b]);
@@ -505,17 +597,23 @@ SpanParams<Real> span_params(Engine* e, int64_t T, int nspans)
 }
 
 template <typename Real>
-rswr_status prepare_tables(Engine* e, const RunReq& r, int* nprobe, cudaStream_t s)
+rswr_status prepare_tables(Engine* e, const RunReq& r, int* nprobe, int64_t* mono_blk_off, cudaStream_t s)
 {
     rswr_status st = upload_problems<Real>(e, r, s);
     if (st != RSWR_OK) return st;
-    return upload_probes<Real>(e, r, nprobe, s);
+    bool dirty = false;
+    if ((st = upload_probes<Real>(e, r, nprobe, &dirty, s)) != RSWR_OK) return st;
+    if ((st = upload_sources<Real>(e, r, &dirty, mono_blk_off, s)) != RSWR_OK) return st;
+    if (dirty)
+        RSWR_CUDA(cudaMemcpyAsync(e->d_tiles, e->h_tiles.data(), sizeof(TileDev) * e->h_tiles.size(),
+                                  cudaMemcpyHostToDevice, s));
+    return RSWR_OK;
 }
 
 // The device work of one run (capturable in a CUDA graph: no host sync, no
 // host-to-device copies).
 template <typename Real>
-rswr_status device_work(Engine* e, const RunReq& r, int nprobe, cudaStream_t s)
+rswr_status device_work(Engine* e, const RunReq& r, int nprobe, int64_t mono_blk_off, cudaStream_t s)
 {
     const size_t es = sizeof(Real);
     rswr_status st = RSWR_OK;
@@ -573,6 +671,10 @@ rswr_status device_work(Engine* e, const RunReq& r, int nprobe, cudaStream_t s)
         mp.nx = ph.nx;
         mp.fA = static_cast<const Real*>(r.fA);
         mp.fB = static_cast<const Real*>(r.fB);
+        if (mono_blk_off >= 0) {
+            mp.srcs = static_cast<const SrcDev<Real>*>(e->d_srcs);
+            mp.blk_src = reinterpret_cast<const int32_t*>(static_cast<const char*>(e->d_srcs) + mono_blk_off);
+        }
         mp.c2 = sizeof(Real) == 8 ? (Real)ph.c2 : (Real)ph.c2f;
         mp.k = sizeof(Real) == 8 ? (Real)ph.k : (Real)ph.kf;
         Real* a = static_cast<Real*>(e->q0[0]);
@@ -617,7 +719,8 @@ std::vector<int64_t> run_key(const Engine* e, const RunReq& r)
     std::vector<int64_t> k{r.mono, P(r.fA), P(r.fB), r.T, P(r.q0), P(r.q1), P(r.out0), P(r.out1), P(r.src),
                            r.src_pitch, r.src_stride, e->variant, e->mode, e->S, e->H, P(e->ev_start),
                            P(e->ev_stop), e->inject_tile, e->inject_span, (int64_t)(e->wait_s * 1e3),
-                           (int64_t)r.probes.size()};
+                           (int64_t)r.probes.size(), r.user_src ? (int64_t)e->usrc.size() : -1, P(e->d_srcs),
+                           e->srcs_live};
     for (const ProbeReq& q : r.probes) {
         k.insert(k.end(), {q.p, q.j, q.kind, P(q.out), q.stride, q.nmax, q.scale_is_c2});
         int64_t sb;
@@ -629,9 +732,10 @@ std::vector<int64_t> run_key(const Engine* e, const RunReq& r)
 }
 
 template <typename Real>
-rswr_status run_graph(Engine* e, const RunReq& r, int nprobe, cudaStream_t s)
+rswr_status run_graph(Engine* e, const RunReq& r, int nprobe, int64_t mono_blk_off, cudaStream_t s)
 {
     std::vector<int64_t> key = run_key(e, r);
+    key.push_back(mono_blk_off);
     if (!e->graph_exec || key != e->graph_key) {
         if (e->graph_exec) {
             cudaGraphExecDestroy(e->graph_exec);
@@ -639,7 +743,7 @@ rswr_status run_graph(Engine* e, const RunReq& r, int nprobe, cudaStream_t s)
         }
         e->graph_key.clear();
         RSWR_CUDA(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
-        rswr_status st = device_work<Real>(e, r, nprobe, e->cap_stream);
+        rswr_status st = device_work<Real>(e, r, nprobe, mono_blk_off, e->cap_stream);
         cudaGraph_t g = nullptr;
         cudaError_t ce = cudaStreamEndCapture(e->cap_stream, &g);
         if (st != RSWR_OK) {
@@ -663,10 +767,11 @@ template <typename Real>
 rswr_status run_impl(Engine* e, const RunReq& r, cudaStream_t s)
 {
     int nprobe = 0;
-    rswr_status st = prepare_tables<Real>(e, r, &nprobe, s);
+    int64_t mono_blk_off = -1;
+    rswr_status st = prepare_tables<Real>(e, r, &nprobe, &mono_blk_off, s);
     if (st != RSWR_OK) return st;
-    if (e->use_graph) return run_graph<Real>(e, r, nprobe, s);
-    return device_work<Real>(e, r, nprobe, s);
+    if (e->use_graph) return run_graph<Real>(e, r, nprobe, mono_blk_off, s);
+    return device_work<Real>(e, r, nprobe, mono_blk_off, s);
 }
 
 rswr_status run_engine(Engine* e, const RunReq& r, cudaStream_t s)
@@ -772,9 +877,33 @@ rswr_status plan_run(Engine* e, const void* fA, const void* fB, int64_t T, const
     r.out0 = out0;
     r.out1 = out1;
     r.mono = mono;
+    r.user_src = true;
     if (traces) add_trace_probes(ph, 0, traces, T, e->esize(), r.probes);
     if (recv) r.probes.push_back(ProbeReq{0, j_r, 0, 1.0, recv, 1, T});
     return run_engine(e, r, static_cast<cudaStream_t>(stream));
+}
+
+rswr_status set_sources(Engine* e, int64_t nsrc, const int32_t* problem, const int64_t* j, const void* samples,
+                        int64_t pitch)
+{
+    if (nsrc < 0 || nsrc > ((int64_t)1 << 24)) return fail(RSWR_EINVAL, "source count out of range");
+    std::vector<Engine::UserSrc> v;
+    if (nsrc > 0) {
+        if (!j || !samples) return fail(RSWR_EINVAL, "points and samples are required");
+        if (pitch < 1) return fail(RSWR_EINVAL, "sample pitch must be >= 1");
+        if (reinterpret_cast<uintptr_t>(samples) % e->esize()) return fail(RSWR_EINVAL, "misaligned samples");
+        v.reserve(nsrc);
+        for (int64_t q = 0; q < nsrc; ++q) {
+            const int64_t p = problem ? problem[q] : 0;
+            if (p < 0 || p >= (int64_t)e->probs.size()) return fail(RSWR_EINVAL, "source problem out of range");
+            if (j[q] < 0 || j[q] >= e->probs[p].nx) return fail(RSWR_EINVAL, "source point outside the grid");
+            v.push_back(Engine::UserSrc{p, j[q], q});
+        }
+    }
+    e->usrc = std::move(v);
+    e->usrc_samples = nsrc > 0 ? samples : nullptr;
+    e->usrc_pitch = nsrc > 0 ? pitch : 0;
+    return RSWR_OK;
 }
 
 // dL/dfA of a receiver-trace functional: the adjoint variables run forward in
@@ -1571,6 +1700,13 @@ rswr_status rswr_plan_set_checkpoint_spacing(rswr_plan_t plan, int64_t spans)
     return RSWR_OK;
 }
 
+rswr_status rswr_plan_set_sources(rswr_plan_t plan, int64_t nsrc, const int64_t* j, const void* samples,
+                                  int64_t pitch)
+{
+    if (!plan) return fail(RSWR_EINVAL, "NULL plan");
+    return set_sources(plan->e, nsrc, nullptr, j, samples, pitch);
+}
+
 rswr_status rswr_plan_inject_missing_flag(rswr_plan_t plan, int32_t tile, int32_t span)
 {
     if (!plan) return fail(RSWR_EINVAL, "NULL plan");
@@ -1665,6 +1801,7 @@ rswr_status rswr_adjoint(rswr_plan_t plan, const void* fA, const void* fB, int64
     if (T < 0) return fail(RSWR_EINVAL, "T < 0");
     if (!wbar || !grad_fA) return fail(RSWR_EINVAL, "wbar and grad_fA are required");
     if (j_r < 0 || j_r >= e->probs[0].nx) return fail(RSWR_EINVAL, "receiver index outside the grid");
+    if (!e->usrc.empty()) return fail(RSWR_ENOTSUP, "the adjoint runs without user point sources");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (grad_a) return adjoint_dispatch(e, T, &j_r, fA, fB, wbar, grad_fA, grad_a, s);
     return adjoint_g(e, T, &j_r, wbar, grad_fA, s);
@@ -1752,6 +1889,14 @@ rswr_status rswr_batch_check(rswr_batch_t batch, void* stream, int32_t* code, in
     return check_engine(batch->e, static_cast<cudaStream_t>(stream), code, tile, span);
 }
 
+rswr_status rswr_batch_set_sources(rswr_batch_t batch, int64_t nsrc, const int32_t* problem, const int64_t* j,
+                                   const void* samples, int64_t pitch)
+{
+    if (!batch) return fail(RSWR_EINVAL, "NULL batch");
+    if (nsrc > 0 && !problem) return fail(RSWR_EINVAL, "problem indices are required");
+    return set_sources(batch->e, nsrc, problem, j, samples, pitch);
+}
+
 rswr_status rswr_batch_run(rswr_batch_t batch, const void* fA, const void* fB, int64_t T, const void* q0,
                            const void* q1, void* out0, void* out1, const int64_t* j_r, void* recv, void* stream)
 {
@@ -1767,6 +1912,7 @@ rswr_status rswr_batch_run(rswr_batch_t batch, const void* fA, const void* fB, i
     r.q1 = q1;
     r.out0 = out0;
     r.out1 = out1;
+    r.user_src = true;
     if (recv && j_r) {
         for (size_t p = 0; p < e->probs.size(); ++p) {
             if (j_r[p] < 0) continue;
@@ -1786,6 +1932,7 @@ rswr_status rswr_batch_adjoint(rswr_batch_t batch, const void* fA, const void* f
     if (T < 0 || !j_r || !wbar || !grad_fA) return fail(RSWR_EINVAL, "bad argument");
     for (size_t p = 0; p < e->probs.size(); ++p)
         if (j_r[p] < 0 || j_r[p] >= e->probs[p].nx) return fail(RSWR_EINVAL, "receiver index outside the grid");
+    if (!e->usrc.empty()) return fail(RSWR_ENOTSUP, "the adjoint runs without user point sources");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (grad_a) return adjoint_dispatch(e, T, j_r, fA, fB, wbar, grad_fA, grad_a, s);
     return adjoint_g(e, T, j_r, wbar, grad_fA, s);
@@ -1827,6 +1974,7 @@ rswr_status rswr_run_paper(rswr_plan_t plan, const void* fA, const void* fB, int
     if (!out0 || !out1) return fail(RSWR_EINVAL, "out0 and out1 are required");
     const ProbHost& ph = e->probs[0];
     if (ph.ov + 64 > 2048) return fail(RSWR_EINVAL, "paper-literal path supports overlaps up to 1984 points");
+    if (!e->usrc.empty()) return fail(RSWR_ENOTSUP, "the paper-literal path runs without user point sources");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (e->dtype == kF64)
         return run_paper<double>(e, static_cast<const double*>(fA), static_cast<const double*>(fB), T,

@@ -36,6 +36,18 @@ struct TileDev {
     int32_t local;        // tile index within its problem (core starts at local * core)
     int32_t probe_begin;  // probes whose point lies in this tile's core
     int32_t probe_end;
+    int32_t src_begin;    // user point sources whose point lies in this tile's window
+    int32_t src_end;      // (halo included), in the caller's order
+};
+
+// A user point source (the pulse sources of the paper's Sec. 4 experiments):
+// when level n+1 of point j is formed, samples[n+1] is added to it (canonical
+// form) or to its increment v^{n+1}, which then re-forms u^{n+1} (increment
+// form).  Sources at one point apply in the caller's order.
+template <typename Real>
+struct SrcDev {
+    int64_t j;            // problem coordinate of the point (0 < j < nx-1)
+    const Real* samples;  // level-n sample at samples[n], n = 0..T
 };
 
 // A per-level sample of the state: kind 0 records u_j * scale, kind 1 records
@@ -55,6 +67,7 @@ struct SpanParams {
     const ProblemDev<Real>* problems;
     const TileDev* tiles;
     const ProbeDev<Real>* probes;
+    const SrcDev<Real>* srcs;  // user sources, grouped by tile (TileDev::src_begin/src_end)
     Real* q0[2];  // ping-pong state: [buffer] first component (u^n)
     Real* q1[2];  // second component (u^{n-1} canonical, v^n increment)
     int64_t ntiles;
@@ -89,6 +102,8 @@ struct MonoParams {
     int64_t n;         // level of `cur`
     const Real* fA;
     const Real* fB;
+    const SrcDev<Real>* srcs;   // user sources sorted by point (stable: same-point order kept)
+    const int32_t* blk_src;     // [grid + 1]: the sources of step-kernel block b are [blk_src[b], blk_src[b+1])
     Real c2;
     Real k;
 };
@@ -205,6 +220,7 @@ cudaError_t paper_resolve_launch(int dtype, const void* params, int ntiles, size
 void set_error_message(const char* m);
 
 // mono_kernel.cu
+constexpr int kMonoBlockPoints = 1024;  // grid points per block of the monolithic step kernel
 cudaError_t mono_launch(int dtype, const void* params, cudaStream_t s);
 cudaError_t probe_final_launch(int dtype, const void* probes, int nprobe, const void* q0, int64_t level,
                                cudaStream_t s);

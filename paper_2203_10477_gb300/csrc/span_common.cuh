@@ -192,6 +192,24 @@ __device__ __forceinline__ void patch_special(Real (&u)[P], Real (&w)[P], const 
     }
 }
 
+// One point source at register r after a step: the sample s is added to the
+// new value (canonical form) or to the new increment, which then re-forms the
+// value from the level-n value uold (increment form).
+template <typename Real, int FORM, int P>
+__device__ __forceinline__ void add_source_at(Real (&u)[P], Real (&w)[P], int r, Real s, Real uold)
+{
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        if (i != r) continue;
+        if constexpr (FORM == kIncrement) {
+            w[i] = radd(w[i], s);
+            u[i] = radd(uold, w[i]);
+        } else {
+            u[i] = radd(u[i], s);
+        }
+    }
+}
+
 // The same step as exchange() + leap_step(), reordered to hide the halo
 // latency: the thread posts its edge values (shuffles + shared slots), updates
 // its interior points 1..P-2, waits at the block barrier, then fetches the

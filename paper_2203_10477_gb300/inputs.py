@@ -25,6 +25,12 @@ these five workloads stand in for them:
           target trace produced with a=1.0 on the same grid and time step.
 * ``c5``  nx=2**28, N=8192, overlap 64, 2**15 steps, plus 512 uneven problems
           with nx in [2**12, 2**20] carrying boundary-waveform gradients.
+
+The paper's N = 10 experiment (Sec. 4) inserts ten pulse sources and splits
+the domain into ten subdomains without stating where the sources sit or what
+they emit; ``pulse_sources`` / ``pulse_experiment`` fix that choice (one
+Gaussian pulse at the centre of each of K equal cells, staggered onsets,
+random amplitudes).
 """
 from __future__ import annotations
 
@@ -193,3 +199,33 @@ def c5_uneven(P: int = 512, T: int = 1 << 15, seed: int = SEED + 5, cfl: float =
                            np.zeros(T + 1), meta={"name": f"c5u[{p}]", "cfl": cfl, "j_r": jr,
                                                   "a_target": 0.8 * ap}))
     return out
+
+
+def pulse_sources(nx: int, T: int, dt: float, K: int = 10, seed: int = SEED + 10,
+                  sigma_steps: float = 30.0) -> tuple[np.ndarray, np.ndarray]:
+    """K interior pulse sources.  Source q sits at j_q = floor((q + 1/2)(nx - 1)/K),
+    the centre of the q-th of K equal cells, and emits
+    A_q / sigma_steps * exp(-((t - t_q)/sigma)^2) with sigma = sigma_steps*dt,
+    t_q = (4 + 2 s_q) sigma; s_q uniform in [0, 1), A_q uniform in [-1, 1]
+    (draw order: all s, then all A).  Returns (j[K] int64, samples[K, T+1])."""
+    r = rng(seed)
+    s = r.uniform(0.0, 1.0, size=K)
+    A = r.uniform(-1.0, 1.0, size=K)
+    t = times(T, dt)
+    sigma = sigma_steps * dt
+    j = np.array([((2 * q + 1) * (nx - 1)) // (2 * K) for q in range(K)], dtype=np.int64)
+    samples = np.empty((K, T + 1))
+    for q in range(K):
+        samples[q] = A[q] / sigma_steps * np.exp(-(((t - (4.0 + 2.0 * s[q]) * sigma) / sigma) ** 2))
+    return j, samples
+
+
+def pulse_experiment(nx: int = 1 << 24, T: int = 10_000, K: int = 10) -> tuple[Problem, np.ndarray, np.ndarray]:
+    """The N = 10 pulse-source experiment: a=1 on [0, 1], CFL 0.9, N = 10
+    subdomains, overlap 64, zero Dirichlet data, K pulse sources from
+    ``pulse_sources``.  Returns (problem, j, samples)."""
+    a, cfl = 1.0, 0.9
+    dt = dt_for_cfl(nx, a, cfl)
+    j, samples = pulse_sources(nx, T, dt, K)
+    return (Problem(nx, a, dt, T, 10, 64, np.zeros(T + 1), np.zeros(T + 1),
+                    meta={"name": "pulse10", "cfl": cfl, "sources": K}), j, samples)

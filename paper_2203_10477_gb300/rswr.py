@@ -74,6 +74,7 @@ SIGNATURES = {
     "rswr_plan_set_mode": (_st, [_vp, _i32]),
     "rswr_plan_set_wait_limit": (_st, [_vp, _dbl]),
     "rswr_plan_set_checkpoint_spacing": (_st, [_vp, _i64]),
+    "rswr_plan_set_sources": (_st, [_vp, _i64, _vp, _vp, _i64]),
     "rswr_plan_inject_missing_flag": (_st, [_vp, _i32, _i32]),
     "rswr_plan_autotune": (_st, [_vp, _i64, ctypes.POINTER(_i32), _vp]),
     "rswr_plan_set_kernel_events": (_st, [_vp, _vp, _vp]),
@@ -81,6 +82,7 @@ SIGNATURES = {
     "rswr_batch_set_graph": (_st, [_vp, _i32]),
     "rswr_batch_autotune": (_st, [_vp, _i64, ctypes.POINTER(_i32), _vp]),
     "rswr_batch_set_kernel_events": (_st, [_vp, _vp, _vp]),
+    "rswr_batch_set_sources": (_st, [_vp, _i64, _vp, _vp, _vp, _i64]),
     "rswr_plan_check": (_st, [_vp, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "rswr_run": (_st, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "rswr_run_host": (_st, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
@@ -169,6 +171,27 @@ def _as_dev(x, dtype: int, device):
     return t.contiguous()
 
 
+def _set_sources(call, dtype, device, problem, j, samples):
+    # marshals a source set; returns the device tensors the library reads (kept by the caller)
+    torch = _torch()
+    if j is None or len(j) == 0:
+        check(call(0, None, None, 0) if problem is None else call(0, None, None, None, 0))
+        return None
+    jj = np.ascontiguousarray(np.asarray(j, dtype=np.int64).reshape(-1))
+    sm = _as_dev(samples, dtype, device)
+    if sm.dim() != 2 or sm.shape[0] != jj.size:
+        raise ValueError("samples must be a 2-D array with one row per source")
+    sm = sm.contiguous()
+    if problem is None:
+        check(call(int(jj.size), jj.ctypes.data, _ptr(sm), int(sm.stride(0))))
+        return sm
+    pp = np.ascontiguousarray(np.asarray(problem, dtype=np.int32).reshape(-1))
+    if pp.size != jj.size:
+        raise ValueError("one problem index per source")
+    check(call(int(jj.size), pp.ctypes.data, jj.ctypes.data, _ptr(sm), int(sm.stride(0))))
+    return sm
+
+
 def variants() -> list[dict]:
     out = []
     for v in range(lib().rswr_variant_count()):
@@ -234,6 +257,12 @@ class Plan:
 
     def set_graph(self, enable: bool):
         check(lib().rswr_plan_set_graph(self.h, int(enable)))
+
+    def set_sources(self, j=None, samples=None):
+        """Point sources: source q at grid point j[q] with samples[q, n] (n = 0..T) added when level n
+        is formed (rswr_plan_set_sources).  samples: a 2-D array, copied to the plan's device; None clears."""
+        self._src_keep = _set_sources(lambda *a: lib().rswr_plan_set_sources(self.h, *a), self.dtype,
+                                      self.device, None, j, samples)
 
     def inject_missing_flag(self, tile: int, span: int):
         check(lib().rswr_plan_inject_missing_flag(self.h, tile, span))
@@ -386,6 +415,12 @@ class Batch:
 
     def set_checkpoint_spacing(self, spans: int):
         check(lib().rswr_batch_set_checkpoint_spacing(self.h, spans))
+
+    def set_sources(self, problem=None, j=None, samples=None):
+        """Point sources of the batch: source q belongs to problem[q] and sits at its point j[q]
+        (rswr_batch_set_sources); samples as in Plan.set_sources."""
+        self._src_keep = _set_sources(lambda *a: lib().rswr_batch_set_sources(self.h, *a), self.dtype,
+                                      self.device, problem, j, samples)
 
     def set_graph(self, enable: bool):
         check(lib().rswr_batch_set_graph(self.h, int(enable)))
