@@ -57,7 +57,8 @@ def load_peaks() -> dict:
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_span_kernel_c2.md")
-KERNEL_SOURCES = ["span_kernel.cu", "span_common.cuh", "rswr_device.cuh", "rswr_internal.h"]
+# the sources of the span kernels a run without point sources executes
+KERNEL_SOURCES = ["span_kernel.cuh", "span_kernel.cu", "span_common.cuh", "rswr_device.cuh", "rswr_internal.h"]
 
 
 def kernel_sha() -> str:
@@ -564,6 +565,43 @@ def bench_paper_literal(torch, dev, T=2000):
     return res
 
 
+def bench_pulse10(torch, dev, T=10_000):
+    """The N = 10 pulse-source experiment (Sec. 4) on a 2^24-point grid: N = 10
+    subdomains, overlap 64, CFL 0.9, zero Dirichlet data, ten Gaussian pulse
+    sources at the centres of ten equal cells (inputs.pulse_experiment).  RSWR
+    (FP64 canonical, FP32 increment) against the monolithic solve with the same
+    sources; the two final states are compared bit for bit on the device."""
+    from paper_2203_10477_gb300 import rswr
+
+    p, j, s = inputs.pulse_experiment(nx=1 << 24, T=T)
+    res = {"workload": "pulse10: nx=2^24, N=10 subdomains, overlap 64, CFL 0.9, 10^4 steps, 10 pulse sources",
+           "unit": UNIT, "sources": [int(x) for x in j]}
+    lups = (p.nx - 2) * p.T
+    for name, dtype, ops in (("f64", rswr.F64, 3), ("f32", rswr.F32, 4)):
+        plan = rswr.Plan.from_problem(p, dtype=dtype, device=dev)
+        td = torch.float64 if dtype == rswr.F64 else torch.float32
+        plan.autotune(64)
+        plan.set_sources(j, torch.as_tensor(s, device=dev).to(td))
+        out = (torch.empty(p.nx, dtype=td, device=dev), torch.empty(p.nx, dtype=td, device=dev))
+        ref = (torch.empty(p.nx, dtype=td, device=dev), torch.empty(p.nx, dtype=td, device=dev))
+        run = lambda: plan.run(None, None, p.T, out=out)
+        mono = lambda: plan.mono(None, None, p.T, out=ref)
+        run()
+        ms = min(_time(torch, run, 2))
+        mono()
+        ms_mono = min(_time(torch, mono, 1))
+        plan.check()
+        v = lups / (ms / 1e3) / 1e9
+        info = plan.info()
+        res[name] = {"value": v, "ms_per_run": ms, "monolithic": lups / (ms_mono / 1e3) / 1e9,
+                     "monolithic_ms": ms_mono, "bitwise_equal_to_monolithic": bool(torch.equal(out[0], ref[0])
+                                                                                   and torch.equal(out[1], ref[1])),
+                     "max_abs_u": float(out[0].abs().max()), "variant": info["variant"],
+                     "span_steps": info["span_steps"], "roofline": alu_roofline(name, v, ops)}
+        del out, ref
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -737,6 +775,8 @@ def main():
         line["large_batch"] = bench_c5_batch(torch, rank, world, dist, dev)
         torch.cuda.empty_cache()
         line["paper_literal"] = bench_paper_literal(torch, dev)
+        torch.cuda.empty_cache()
+        line["pulse10"] = bench_pulse10(torch, dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
     if rank == 0:
