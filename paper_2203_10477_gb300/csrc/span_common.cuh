@@ -473,15 +473,22 @@ __device__ __forceinline__ void warp_neighbours(const Real (&u)[P], Real& lft, R
 // shuffles of their new values for the next step, then the interior points,
 // so that the shuffle latency hides behind the interior updates.  Every update
 // is the same expression on the same operands as leap_step(), so the bits are
-// identical.
-template <typename Real, int FORM, int P>
+// identical.  `rec(u, lft, rgt, s)` sees every level s = 0 .. steps-1 with its
+// neighbours before it is advanced (probe recording; it must not shuffle).
+struct NoRecord {
+    template <typename U, typename Real>
+    __device__ __forceinline__ void operator()(const U&, Real, Real, int) const {}
+};
+
+template <typename Real, int FORM, int P, typename Rec = NoRecord>
 __device__ __forceinline__ void warp_steps_edges_first(Real (&u)[P], Real (&w)[P], Real c2, Real k, int steps,
-                                                       int lane)
+                                                       int lane, Rec rec = Rec{})
 {
     static_assert(P >= 3, "edges-first order needs interior points");
     Real lft, rgt;
     warp_neighbours<Real, P>(u, lft, rgt, lane);
     for (int s = 0; s < steps; ++s) {
+        rec(u, lft, rgt, s);
         Real n0, nl, v0, vl;  // new first / last point and their second components
         Real d0 = Real(0);
         if constexpr (FORM == kIncrement) {

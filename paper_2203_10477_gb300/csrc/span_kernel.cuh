@@ -287,10 +287,25 @@ __device__ __forceinline__ void predict_tile(const SpanParams<Real>& prm, const 
             wsrc = __any_sync(kFull, sp.rs >= 0);
             reload(0, true);
         }
-        if constexpr (KH > 0 && !PR && !SP) {
-            // plain interior tile of a warp window: the bare stencil, edges first
-            warp_steps_edges_first<Real, FORM, P>(u, w, c2, kk, s_end - s_begin, lane);
-            return;
+        if constexpr (KH > 0 && !SP) {
+            if constexpr (!PR) {
+                // plain interior tile of a warp window: the bare stencil, edges first
+                warp_steps_edges_first<Real, FORM, P>(u, w, c2, kk, s_end - s_begin, lane);
+                return;
+            } else {
+                // interior tile with probes: edges first as well, each level
+                // recorded by its owner before it is advanced
+                if (!many_probes) {
+                    warp_steps_edges_first<Real, FORM, P>(
+                        u, w, c2, kk, s_end - s_begin, lane, [&](const Real(&uu)[P], Real l, Real r, int s) {
+                            if (nown > 0) record_step<Real, P>(op0, uu, l, r, s);
+                            if (nown > 1) record_step<Real, P>(op1, uu, l, r, s);
+                            for (uint32_t m = more; m != 0u; m &= m - 1u)
+                                record_owned<Real, P>(uu, l, r, tprobes[__ffs(m) - 1], wabs, tb, n0 + s_begin + s);
+                        });
+                    return;
+                }
+            }
         }
         for (int s = s_begin; s < s_end; ++s) {
             Real lft, rgt;
