@@ -68,3 +68,14 @@ def test_validation_errors_are_reported_without_touching_the_device(built_lib):
     assert L.rswr_plan_create(ctypes.byref(h), 0.0, 1.0, 1.0, 2, 0.005, 1, 2, 1, 0, 0) == 1
     assert L.rswr_plan_create(ctypes.byref(h), 0.0, 1.0, 1.0, 101, 0.005, 2, 8, 7, 0, 0) == 1
     assert L.rswr_plan_create(None, 0.0, 1.0, 1.0, 101, 0.005, 2, 8, 1, 0, 0) == 1
+
+
+def test_source_setters_reject_null_handles_without_touching_the_device(built_lib):
+    from paper_2203_10477_gb300 import rswr
+
+    L = rswr.lib()
+    j = (ctypes.c_int64 * 1)(5)
+    p = (ctypes.c_int32 * 1)(0)
+    assert L.rswr_plan_set_sources(None, 1, j, None, 8) == 1
+    assert L.rswr_batch_set_sources(None, 1, p, j, None, 8) == 1
+    assert b"NULL" in L.rswr_last_error_message()

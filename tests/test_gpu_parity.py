@@ -674,3 +674,32 @@ def test_paper_literal_fp32_close_to_fp64(R, oracle_mod):
     err = np.abs(host(got["u"]).astype(np.float64) - mono["u"]).max() / np.abs(mono["u"]).max()
     assert err <= 1e-5, err
     assert got["spans"].sum() == T
+
+
+@pytest.mark.parametrize("dtype,form", [(F64, CAN), (F32, INC), (F32, CAN), (F64, INC)])
+@pytest.mark.parametrize("nx,N,ov,T,jr", [
+    (20011, 1000, 8, 150, 10007),   # interfaces every 20 points: hundreds of probes per tile
+    (8001, 20, 4, 200, 399),        # probes 3 apart next to the receiver: several per thread
+])
+def test_dense_interface_traces_every_variant(R, oracle_mod, dtype, form, nx, N, ov, T, jr):
+    """Interface output waveforms where a tile or a thread holds many probes
+    (the tile-list and the per-thread overflow recording paths), every variant."""
+    dt = 0.9 / (nx - 1)
+    fA = inputs.ramped_sine(T, dt, freq=60.0) + 0.2
+    q0 = inputs.smooth_random_state(nx, seed=17)
+    dt_ = np.float64 if dtype == F64 else np.float32
+    ref = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, np.zeros(T + 1), form=ORACLE_FORM[form], prec=prec(dtype),
+                              q0=q0.astype(dt_), rec_j=[jr])
+    rs = oracle_mod.rswr_mask(nx, T, 1.0, dt, fA, np.zeros(T + 1), N, ov, form=ORACLE_FORM[form], prec=prec(dtype),
+                              q0=q0.astype(dt_))
+    plan = R.Plan(0.0, 1.0, 1.0, nx, dt, N, ov, dtype=dtype, form=form)
+    for v in [v for v in R.variants() if v["dtype"] == dtype and v["form"] == form]:
+        plan.set_variant(v["variant"])
+        for mode in (0, 1):
+            plan.set_mode(mode)
+            out = plan.run(fA, None, T, q0=q0, traces=True, j_r=jr)
+            plan.check()
+            what = f"variant {v['variant']} mode {mode}"
+            assert_bitwise(host(out["u"]), ref["u"], what)
+            assert_bitwise(host(out["recv"]), ref["rec"][0], what + " receiver")
+            assert_bitwise(host(out["traces"]), rs["traces"], what + " traces")
