@@ -32,24 +32,6 @@ namespace {
 
 using namespace span;
 
-template <typename Real, int P>
-__device__ __forceinline__ Special special_points(int64_t gj, int64_t nx, int64_t js)
-{
-    Special sp{-1, -1, -1, 0, P - 1};
-    auto loc = [&](int64_t j) -> int { return (j >= gj && j < gj + P) ? (int)(j - gj) : -1; };
-    sp.r0 = loc(0);
-    sp.r1 = loc(nx - 1);
-    sp.rs = js >= 0 ? loc(js) : -1;
-    sp.rlo = (int)(gj >= 0 ? 0 : (-gj > P ? P : -gj));
-    sp.rhi = (int)(nx - 1 - gj >= P - 1 ? P - 1 : (nx - 1 - gj < -1 ? -1 : nx - 1 - gj));
-    return sp;
-}
-
-__device__ __forceinline__ bool is_special(const Special& sp, int P)
-{
-    return sp.r0 >= 0 || sp.r1 >= 0 || sp.rs >= 0 || sp.rlo > 0 || sp.rhi < P - 1;
-}
-
 // Geometry and data of one adjoint tile.
 template <typename Real>
 struct AdjTile {
@@ -102,8 +84,8 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
         Real u[P], w[P];
         smem_to_regs<Real, P>(stage + 0 * W + tid * P, u);
         smem_to_regs<Real, P>(stage + 1 * W + tid * P, w);
-        const Special sp = special_points<Real, P>(gj, nx, -1);
-        const bool special = edge && is_special(sp, P);
+        const Special sp = make_special<P>(gj, nx, -1);
+        const bool special = edge && any_special(sp);
         // Dirichlet samples of the span through the warp (warp-uniform choices)
         WarpChunk<Real> ca{}, cb{};
         bool wa = false, wb = false;
@@ -184,8 +166,8 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
     Real l[P], lw[P];
     smem_to_regs<Real, P>(stage + 2 * W + tid * P, l);
     smem_to_regs<Real, P>(stage + 3 * W + tid * P, lw);
-    const Special sp = special_points<Real, P>(gj, nx, has_src ? pl.js : -1);
-    const bool special = (edge || has_src) && is_special(sp, P);
+    const Special sp = make_special<P>(gj, nx, has_src ? pl.js : -1);
+    const bool special = (edge || has_src) && any_special(sp);
     // the source samples (cotangent) of the span through the warp: level m0 + 1 + i
     WarpChunk<Real> cs{};
     bool wsrc = false;
@@ -228,7 +210,7 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
         }
         if (special) {
             // the increment form adds the source to v before u' = u + v: keep u
-            const Real uold = (FORM == kIncrement && sp.rs >= 0) ? select_reg<Real, P>(l, sp.rs) : Real(0);
+            const Real uold = (FORM == kIncrement && sp.rs >= 0) ? reg_get<Real, P>(l, sp.rs) : Real(0);
             leap_step<Real, FORM, P>(l, lw, lft, rgt, c2, kk);
             patch_special<Real, FORM, P>(l, lw, sp, uold, sval, Real(0), Real(0), Real(0), Real(0));
         } else {

@@ -4,6 +4,8 @@
 // patches and the per-level probes.
 #pragma once
 
+#include <type_traits>
+
 #include "rswr_internal.h"
 
 namespace rswr {
@@ -142,53 +144,100 @@ __device__ __forceinline__ Real level_sample(const Real* a, int64_t stride, int6
     return (a != nullptr && level >= 0 && level <= nmax) ? a[level * stride] : Real(0);
 }
 
-// Points of a thread that need more than the stencil: the Dirichlet nodes
-// (local index r0 -> j = 0, r1 -> j = nx-1), the point source (rs) and points
-// outside [0, nx) (local indices outside [rlo, rhi]).  -1 = not owned.
+// Points of a thread that need more than the stencil (register index, -1 = not
+// held): the Dirichlet nodes (r0: j = 0, r1: j = nx-1), the point source (rs)
+// and the two points outside the grid next to the nodes (rm: j = -1, rp: j = nx).
+// Every other point outside [0, nx) keeps the value 0 by itself: it starts at 0
+// (state arrays and pads are zeroed) and so do its neighbours, and a 3-point
+// update of zeros is an exact 0 in both forms.  Only rm and rp, whose update
+// reads a node, are reset after each step, so outside points stay 0 and never
+// reach a grid point.
 struct Special {
-    int r0, r1, rs, rlo, rhi;
+    int r0, r1, rs, rm, rp;
 };
 
-template <typename Real, int P>
-__device__ __forceinline__ Real select_reg(const Real (&u)[P], int r)
+// The special points among the P points from problem coordinate lo on.
+template <int P>
+__device__ __forceinline__ Special make_special(int64_t lo, int64_t nx, int64_t js)
 {
-    Real v = u[0];
-#pragma unroll
-    for (int i = 1; i < P; ++i)
-        if (i == r) v = u[i];
+    auto loc = [&](int64_t j) -> int { return (j >= lo && j < lo + P) ? (int)(j - lo) : -1; };
+    return Special{loc(0), loc(nx - 1), js >= 0 ? loc(js) : -1, loc(-1), loc(nx)};
+}
+
+__device__ __forceinline__ bool any_special(const Special& sp)
+{
+    return sp.r0 >= 0 || sp.r1 >= 0 || sp.rs >= 0 || sp.rm >= 0 || sp.rp >= 0;
+}
+
+// f(I) on register I = r of a register array (I a compile-time constant), by a
+// binary tree of branches over r: log2(P) compares instead of one per register.
+template <int P, int LO = 0, int HI = P, typename F>
+__device__ __forceinline__ void reg_apply(int r, F&& f)
+{
+    if constexpr (HI - LO == 1) {
+        f(std::integral_constant<int, LO>{});
+    } else {
+        constexpr int MID = (LO + HI) / 2;
+        if (r < MID) reg_apply<P, LO, MID>(r, f);
+        else reg_apply<P, MID, HI>(r, f);
+    }
+}
+
+template <typename Real, int P>
+__device__ __forceinline__ Real reg_get(const Real (&u)[P], int r)
+{
+    Real v = Real(0);
+    reg_apply<P>(r, [&](auto I) { v = u[decltype(I)::value]; });
     return v;
 }
 
 // Applied right after leap_step to the thread's special points (step n -> n+1):
 //   source:    canonical u' += s;  increment v' += s, u' = u_old + v'
 //   Dirichlet: u' = f(n+1);  increment v' = f(n+1) - f(n)  (canonical keeps u_prev = f(n))
-//   outside:   u' = 0, second component 0
+//   j = -1, j = nx: u' = 0, second component 0
 template <typename Real, int FORM, int P>
 __device__ __forceinline__ void patch_special(Real (&u)[P], Real (&w)[P], const Special& sp, Real uold_s, Real sval,
                                               Real fa_old, Real fa_new, Real fb_old, Real fb_new)
 {
-#pragma unroll
-    for (int i = 0; i < P; ++i) {
-        if (i == sp.rs) {
+    if (sp.rs >= 0)
+        reg_apply<P>(sp.rs, [&](auto I) {
+            constexpr int i = decltype(I)::value;
             if constexpr (FORM == kIncrement) {
                 w[i] = radd(w[i], sval);
                 u[i] = radd(uold_s, w[i]);
             } else {
                 u[i] = radd(u[i], sval);
             }
-        }
-        if (i == sp.r0) {
+        });
+    // a node and its outside neighbour: the same register tree; the neighbour
+    // sits in the next lane over when the node is the thread's first / last point
+    if (sp.r0 >= 0)
+        reg_apply<P>(sp.r0, [&](auto I) {
+            constexpr int i = decltype(I)::value;
             u[i] = fa_new;
             if constexpr (FORM == kIncrement) w[i] = rsub(fa_new, fa_old);
-        }
-        if (i == sp.r1) {
+            if constexpr (i > 0) {
+                u[i - 1] = Real(0);
+                w[i - 1] = Real(0);
+            }
+        });
+    else if (sp.rm == P - 1) {
+        u[P - 1] = Real(0);
+        w[P - 1] = Real(0);
+    }
+    if (sp.r1 >= 0)
+        reg_apply<P>(sp.r1, [&](auto I) {
+            constexpr int i = decltype(I)::value;
             u[i] = fb_new;
             if constexpr (FORM == kIncrement) w[i] = rsub(fb_new, fb_old);
-        }
-        if (i < sp.rlo || i > sp.rhi) {
-            u[i] = Real(0);
-            w[i] = Real(0);
-        }
+            if constexpr (i < P - 1) {
+                u[i + 1] = Real(0);
+                w[i + 1] = Real(0);
+            }
+        });
+    else if (sp.rp == 0) {
+        u[0] = Real(0);
+        w[0] = Real(0);
     }
 }
 
@@ -198,16 +247,15 @@ __device__ __forceinline__ void patch_special(Real (&u)[P], Real (&w)[P], const 
 template <typename Real, int FORM, int P>
 __device__ __forceinline__ void add_source_at(Real (&u)[P], Real (&w)[P], int r, Real s, Real uold)
 {
-#pragma unroll
-    for (int i = 0; i < P; ++i) {
-        if (i != r) continue;
+    reg_apply<P>(r, [&](auto I) {
+        constexpr int i = decltype(I)::value;
         if constexpr (FORM == kIncrement) {
             w[i] = radd(w[i], s);
             u[i] = radd(uold, w[i]);
         } else {
             u[i] = radd(u[i], s);
         }
-    }
+    });
 }
 
 // The same step as exchange() + leap_step(), reordered to hide the halo

@@ -196,17 +196,7 @@ __device__ __forceinline__ void predict_tile(const SpanParams<Real>& prm, const 
     const bool many_probes = has_probe && !few_probes;
 
     // special points of this thread (edge / source tiles only)
-    auto special_points = [&](int64_t sj) {
-        Special sp{-1, -1, -1, 0, P - 1};
-        const int64_t lo = gj;
-        auto loc = [&](int64_t j) -> int { return (j >= lo && j < lo + P) ? (int)(j - lo) : -1; };
-        sp.r0 = loc(0);
-        sp.r1 = loc(nx - 1);
-        sp.rs = sj >= 0 ? loc(sj) : -1;
-        sp.rlo = (int)(lo >= 0 ? 0 : (-lo > P ? P : -lo));
-        sp.rhi = (int)(nx - 1 - lo >= P - 1 ? P - 1 : (nx - 1 - lo < -1 ? -1 : nx - 1 - lo));
-        return sp;
-    };
+    auto special_points = [&](int64_t sj) { return make_special<P>(gj, nx, sj); };
 
     int buf = 0;
     // steps [s_begin, s_end) of the span; PR: record probes, SP: patch special
@@ -232,7 +222,7 @@ __device__ __forceinline__ void predict_tile(const SpanParams<Real>& prm, const 
                 }
             }
         }
-        Special sp{-1, -1, -1, 0, P - 1};
+        Special sp{-1, -1, -1, -1, -1};
         // boundary and source samples of the span, through the warp (warp-uniform choices):
         // fA / fB at level n0 + s_begin + i, the source at level n0 + s_begin + i + 1
         WarpChunk<Real> ca{}, cb{}, cs{};
@@ -348,11 +338,11 @@ __device__ __forceinline__ void predict_tile(const SpanParams<Real>& prm, const 
                     fb_new = cb.get(dd + 1);
                 }
                 if constexpr (FORM == kIncrement) {
-                    if (sp.rs >= 0) uold_s = select_reg<Real, P>(u, sp.rs);
+                    if (sp.rs >= 0) uold_s = reg_get<Real, P>(u, sp.rs);
                     if (US && multi)
                         for (int q = td.src_begin; q < td.src_end; ++q) {
                             const int64_t li = prm.srcs[q].j - gj;
-                            if (li >= 0 && li < P) uo_m[li] = select_reg<Real, P>(u, (int)li);
+                            if (li >= 0 && li < P) uo_m[li] = reg_get<Real, P>(u, (int)li);
                         }
                 }
                 leap_step<Real, FORM, P>(u, w, lft, rgt, c2, kk);
