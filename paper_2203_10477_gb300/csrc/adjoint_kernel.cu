@@ -102,12 +102,14 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
                 cb.c1 = level_sample(pu.fB, 1, at.n0 + 32 + lane, prm.T);
             }
         }
-        for (int s = 0; s < len; ++s) {
+        // one level: its Laplacian to shared memory and (STEP) the step to the
+        // next level; the last level of the span only stores its Laplacian
+        auto level = [&](auto step_c, int s) {
+            constexpr bool STEP = decltype(step_c)::value;
             Real lft, rgt;
             exchange<Real, P, NW, BAR>(u, lft, rgt, xch, buf, warp, lane);
             buf ^= 1;
             Real* lp = laps + s * W + lap_base;  // point i of this thread at lp[i * lap_stride]
-            const bool step = s + 1 < len;
             // one pass: the Laplacian of this level (from the step's own neighbour
             // sum, (uL + uR) - 2u = fma(-2, u, uL + uR) exactly) and the step
             if constexpr (FORM == kCanonical) {
@@ -118,7 +120,7 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
                     const Real ur = i < P - 1 ? u[i + 1] : rgt;
                     const Real sum = radd(ul, ur);
                     lp[i * lap_stride] = rfma(Real(-2), uc, sum);
-                    if (step) {
+                    if constexpr (STEP) {
                         u[i] = rfma(c2, sum, rfma(kk, uc, -w[i]));
                         w[i] = uc;
                     }
@@ -133,32 +135,38 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
                     const Real lap = rsub(d, d_prev);
                     d_prev = d;
                     lp[i * lap_stride] = lap;
-                    if (step) {
+                    if constexpr (STEP) {
                         const Real v = rfma(c2, lap, w[i]);
                         w[i] = v;
                         u[i] = radd(u[i], v);
                     }
                 }
             }
-            Real fa_old = Real(0), fa_new = Real(0), fb_old = Real(0), fb_new = Real(0);
-            if (s - cbase == 32) {
-                cbase += 32;
-                ca.c0 = ca.c1;
-                cb.c0 = cb.c1;
-                if (wa) ca.c1 = level_sample(pu.fA, 1, at.n0 + cbase + 32 + lane, prm.T);
-                if (wb) cb.c1 = level_sample(pu.fB, 1, at.n0 + cbase + 32 + lane, prm.T);
+            if constexpr (STEP) {
+                // samples through the warp: wa / wb are warp-uniform, so every
+                // lane takes part in the shuffles; only the patch is per thread
+                if (s - cbase == 32) {
+                    cbase += 32;
+                    ca.c0 = ca.c1;
+                    cb.c0 = cb.c1;
+                    if (wa) ca.c1 = level_sample(pu.fA, 1, at.n0 + cbase + 32 + lane, prm.T);
+                    if (wb) cb.c1 = level_sample(pu.fB, 1, at.n0 + cbase + 32 + lane, prm.T);
+                }
+                Real fa_old = Real(0), fa_new = Real(0), fb_old = Real(0), fb_new = Real(0);
+                if (wa) {
+                    fa_old = ca.get(s - cbase);
+                    fa_new = ca.get(s - cbase + 1);
+                }
+                if (wb) {
+                    fb_old = cb.get(s - cbase);
+                    fb_new = cb.get(s - cbase + 1);
+                }
+                if (special)
+                    patch_special<Real, FORM, P>(u, w, sp, Real(0), Real(0), fa_old, fa_new, fb_old, fb_new);
             }
-            if (wa) {
-                fa_old = ca.get(s - cbase);
-                fa_new = ca.get(s - cbase + 1);
-            }
-            if (wb) {
-                fb_old = cb.get(s - cbase);
-                fb_new = cb.get(s - cbase + 1);
-            }
-            if (step && special)
-                patch_special<Real, FORM, P>(u, w, sp, Real(0), Real(0), fa_old, fa_new, fb_old, fb_new);
-        }
+        };
+        for (int s = 0; s + 1 < len; ++s) level(std::true_type{}, s);
+        if (len > 0) level(std::false_type{}, len - 1);
     }
 
     // ---- lambda phase: levels m0 .. m0+len-1 pair with u levels n0+len-1 .. n0
