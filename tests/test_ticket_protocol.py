@@ -17,6 +17,9 @@ overwrite by span k + 2 before the read), that every ticket completes without
 a timeout, and that a tile which never publishes (the host-injected fault of
 rswr_plan_inject_missing_flag) ends the run with a latched error instead of a
 hang.  Waits are bounded by a poll budget, like the kernel's time limit.
+The persistent adjoint sweep (adj_producer in csrc/adjoint_kernel.cu) runs the
+same protocol with its spans taken last first, i.e. the same tickets in
+dependency order, so the model covers it as well.
 """
 from __future__ import annotations
 
