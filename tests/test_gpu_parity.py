@@ -740,3 +740,26 @@ def test_adjoint_matches_central_differences_of_the_gpu_forward(R):
     ha = 1e-6 * a  # the O(h^2) term is about 8e-9 relative here (7e-5 at 1e-4 a)
     fda = (loss(a + ha, g) - loss(a - ha, g)) / (2 * ha)
     assert abs(fda - ga) <= 1e-7 * abs(ga)
+
+
+@pytest.mark.parametrize("dtype,form", [(F64, CAN), (F64, INC), (F32, INC), (F32, CAN)])
+def test_resume_from_a_span_boundary_state(R, dtype, form):
+    """Checkpoint / resume (Sec. 2.6: the span loop restarts from the combined
+    state): a run of T1 steps followed by a run of T - T1 steps from its final
+    state pair, with the boundary samples from level T1 on, equals one run of T
+    steps bit for bit, at a span boundary and off one."""
+    nx, N, ov, T = 6007, 6, 48, 400
+    dt = 0.9 / (nx - 1)
+    fA = inputs.ramped_sine(T, dt, freq=31.0) + 0.1
+    fB = 0.4 * inputs.ramped_sine(T, dt, freq=17.0)
+    q0 = inputs.smooth_random_state(nx, seed=23)
+    plan = R.Plan(0.0, 1.0, 1.0, nx, dt, N, ov, dtype=dtype, form=form)
+    full = plan.run(fA, fB, T, q0=q0)
+    ref_u, ref_w = host(full["u"]), host(full["w"])
+    S = plan.info()["span_steps"]
+    for T1 in (5 * S, 5 * S + 3):
+        a = plan.run(fA[:T1 + 1], fB[:T1 + 1], T1, q0=q0)
+        b = plan.run(fA[T1:], fB[T1:], T - T1, q0=a["u"].clone(), q1=a["w"].clone())
+        plan.check()
+        assert_bitwise(host(b["u"]), ref_u, f"resumed at {T1}: u")
+        assert_bitwise(host(b["w"]), ref_w, f"resumed at {T1}: w")
