@@ -103,6 +103,23 @@ def alu_roofline(dtype: str, value: float, ops: int) -> dict:
             "ops_per_update": ops, "pipe": "fp64" if dtype == "f64" else "fp32"}
 
 
+def span_roofline(dtype: str, value: float, ops: int, info: dict) -> dict:
+    """The binding roofline of a span-kernel run: the lower of the ALU bound
+    (alu_roofline) and the HBM bound at the span kernel's algorithmic bytes per
+    update, w (2 W + 2 core) / (core S) (both levels of every window in, both
+    levels of its core out, once per span of S steps)."""
+    w = 8 if dtype == "f64" else 4
+    W, core, S = info["window"], info["core"], info["span_steps"]
+    bpu = w * (2 * W + 2 * core) / (core * S)
+    hbm = load_peaks()["hbm_gbs"]
+    alu = alu_roofline(dtype, value, ops)
+    hbm_peak = hbm / bpu
+    out = dict(alu, alu_peak=alu["peak"], hbm_peak=hbm_peak, algorithmic_bytes_per_update=bpu)
+    if hbm_peak < alu["peak"]:
+        out.update(bound="hbm", peak=hbm_peak, frac=value / hbm_peak)
+    return out
+
+
 def alu_peaks(sm_mhz: float) -> dict:
     """Arithmetic-pipe-bound LUP rates of the span kernel's fast path.
 
@@ -360,6 +377,21 @@ def profile_case(which: str, variant=None, span=None, full=False, log2_nx=22) ->
     from paper_2203_10477_gb300 import build, rswr
 
     build.build()
+    if which == "c3":
+        # the batched workload's first 1024 problems for 256 steps (16 spans of
+        # 16), FP32, in the bench's configuration (variant, one launch per span)
+        probs = inputs.c3_problems(P=1024, T=256)
+        b = rswr.Batch(probs, dtype=rswr.F32)
+        if variant is not None:
+            b.set_variant(variant)
+        b.set_mode(1)
+        fA = torch.as_tensor(np.concatenate([q.fA for q in probs]), device="cuda").to(torch.float32)
+        for _ in range(2):
+            b.run(fA, None, probs[0].T)
+        torch.cuda.synchronize()
+        b.check()
+        print(json.dumps({"profile_case": which, "problems": len(probs), "T": probs[0].T, "info": b.info()}))
+        return
     if which in ("adj64", "adj32"):
         # the c4 gradient workload (dL/dfA and dL/da), run twice; a smaller grid
         # (log2_nx < 20) scales the steps with it
@@ -440,7 +472,7 @@ def bench_batched(torch, rank, world, dist, dev):
             "value": tot / t / 1e9, "unit": UNIT, "ms_per_run": 1e3 * t, "lups_per_run": tot,
             "variant": info["variant"], "span_steps": info["span_steps"], "mode": info["mode"],
             "sharding": f"{world} rank(s), whole problems per rank",
-            "roofline": alu_roofline("f32", tot / t / 1e9 / world, 4)}
+            "roofline": span_roofline("f32", tot / t / 1e9 / world, 4, info)}
 
 
 def bench_adjoint(torch, dev):
@@ -499,7 +531,7 @@ def bench_large(torch, dev):
     v = lups / (ms[0] / 1e3) / 1e9
     return {"workload": "c5: nx=2^28 FP32, N=8192, overlap 64, 2^15 steps", "value": v,
             "unit": UNIT, "ms_per_run": ms[0], "variant": info["variant"], "span_steps": info["span_steps"],
-            "roofline": alu_roofline("f32", v, 4)}
+            "roofline": span_roofline("f32", v, 4, info)}
 
 
 def bench_c5_batch(torch, rank, world, dist, dev):
@@ -537,9 +569,9 @@ def bench_c5_batch(torch, rank, world, dist, dev):
     return {"workload": "c5: 512 uneven problems, nx U[2^12,2^20], a U[0.5,2], CFL 0.9, overlap 64, 2^15 steps, FP32",
             "unit": UNIT, "lups_per_run": tot,
             "forward": {"value": tot / t_f / 1e9, "ms_per_run": t_f * 1e3,
-                        "roofline": alu_roofline("f32", tot / t_f / 1e9, 4)},
+                        "roofline": span_roofline("f32", tot / t_f / 1e9, 4, info)},
             "adjoint_grad_fA": {"value": tot / t_a / 1e9, "ms_per_run": t_a * 1e3,
-                                "roofline": alu_roofline("f32", tot / t_a / 1e9, 4)},
+                                "roofline": span_roofline("f32", tot / t_a / 1e9, 4, info)},
             "variant": info["variant"], "span_steps": info["span_steps"], "mode": info["mode"],
             "sharding": f"{world} rank(s), whole problems per rank"}
 
@@ -597,7 +629,7 @@ def bench_pulse10(torch, dev, T=10_000):
                      "monolithic_ms": ms_mono, "bitwise_equal_to_monolithic": bool(torch.equal(out[0], ref[0])
                                                                                    and torch.equal(out[1], ref[1])),
                      "max_abs_u": float(out[0].abs().max()), "variant": info["variant"],
-                     "span_steps": info["span_steps"], "roofline": alu_roofline(name, v, ops)}
+                     "span_steps": info["span_steps"], "roofline": span_roofline(name, v, ops, info)}
         del out, ref
     return res
 
@@ -611,8 +643,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mono", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched / adjoint / large-grid measurements")
-    ap.add_argument("--profile-case", choices=["f64", "f32", "adj64", "adj32"], default=None,
-                    help="run the small profiling case (nx=2^22, 1280 steps) twice and exit (for ncu)")
+    ap.add_argument("--profile-case", choices=["f64", "f32", "adj64", "adj32", "c3"], default=None,
+                    help="run a small profiling case twice and exit (for ncu): f64/f32 nx=2^22, 1280 steps; "
+                         "adj64/adj32 the c4 gradient; c3 the first 1024 batched problems, 256 steps")
     ap.add_argument("--variant", type=int, default=None, help="kernel variant of the profiling case")
     ap.add_argument("--profile-log2-nx", type=int, default=None,
                     help="grid of the profiling case: 2^N points (default 22; 24 = the bench grid; "
