@@ -227,7 +227,11 @@ int oracle_rswr_paper(int form, int64_t nx, int64_t T, double c, double c2, doub
     if (nspans) *nspans = m;
     memcpy(out0, u, sizeof(double) * nx);
     memcpy(out1, w, sizeof(double) * nx);
-    free(u); free(w); free(nu); free(nw); free(eu); free(ew); free(tu); free(tw);
+    /* u / nu and w / nw were swapped a whole number of times: free the four
+     * buffers through a list of their current names */
+    double* bufs[4] = {u, w, nu, nw};
+    for (int b = 0; b < 4; ++b) free(bufs[b]);
+    free(eu); free(ew); free(tu); free(tw);
     free(traj); free(gbuf); free(scratch);
     return 0;
 }

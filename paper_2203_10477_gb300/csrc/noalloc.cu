@@ -95,7 +95,7 @@ __global__ void noalloc_tables_kernel(ProblemDev<Real>* prob, TileDev* tiles, De
         err->span = 0;
         err->where = 0;
     }
-    if (i < ntiles) tiles[i] = TileDev{0, (int32_t)i, 0, 0};
+    if (i < ntiles) tiles[i] = TileDev{0, (int32_t)i, 0, 0, 0, 0};
 }
 
 template <typename Real>

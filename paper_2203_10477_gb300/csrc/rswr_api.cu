@@ -196,7 +196,7 @@ rswr_status layout(Engine* e)
         ph.base = at + pad;
         ph.tile0 = tile;
         ph.off = off;
-        for (int64_t t = 0; t < ph.ntiles; ++t) e->h_tiles.push_back(TileDev{(int32_t)p, (int32_t)t, 0, 0});
+        for (int64_t t = 0; t < ph.ntiles; ++t) e->h_tiles.push_back(TileDev{(int32_t)p, (int32_t)t, 0, 0, 0, 0});
         int64_t len = pad + ph.ntiles * e->core + pad;
         len = (len + kAlign - 1) / kAlign * kAlign;
         at += len;
@@ -1092,7 +1092,7 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     std::vector<TileDev> ht;
     ht.reserve(ntf + nta);
     for (int p = 0; p < np; ++p)
-        for (int64_t t = 0; t < tcf[p]; ++t) ht.push_back(TileDev{p, (int32_t)t, 0, 0});
+        for (int64_t t = 0; t < tcf[p]; ++t) ht.push_back(TileDev{p, (int32_t)t, 0, 0, 0, 0});
     std::vector<ProbeDev<Real>> hp;
     std::vector<ProblemDev<Real>> hpr(2 * np);
     std::vector<double> hscale(np);
@@ -1100,7 +1100,7 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
         const ProbHost& ph = e->probs[p];
         const bool interior = j_r[p] > 0 && j_r[p] < ph.nx - 1;
         for (int64_t t = 0; t < tca[p]; ++t) {
-            TileDev td{p, (int32_t)t, (int32_t)hp.size(), (int32_t)hp.size()};
+            TileDev td{p, (int32_t)t, (int32_t)hp.size(), (int32_t)hp.size(), 0, 0};
             if (t == 0 && interior) td.probe_end += 1;  // grid point 1 lies in the first core
             ht.push_back(td);
             if (t == 0 && interior) {
