@@ -763,3 +763,29 @@ def test_resume_from_a_span_boundary_state(R, dtype, form):
         plan.check()
         assert_bitwise(host(b["u"]), ref_u, f"resumed at {T1}: u")
         assert_bitwise(host(b["w"]), ref_w, f"resumed at {T1}: w")
+
+
+def test_c1_equals_the_stored_oracle_values(R):
+    """The GPU run of the golden problem (the c1 grid with a polynomial boundary
+    pulse) against the values stored in tests/golden/c1_fp64.txt (written from
+    the oracle on another machine): final state, receiver and both interface
+    waveforms, bit for bit, with no oracle run in the test."""
+    import os
+    import sys
+
+    here = os.path.dirname(os.path.abspath(__file__))
+    sys.path.insert(0, os.path.join(here, "golden"))
+    import make_golden
+
+    stored = make_golden.read(os.path.join(here, "golden", "c1_fp64.txt"))
+    p = make_golden.problem()
+    plan = R.Plan.from_problem(p, dtype=F64)
+    out = plan.run(p.fA, p.fB, p.T, traces=True, j_r=make_golden.RECV_J)
+    plan.check()
+    u, rec, tr = host(out["u"]), host(out["recv"]), host(out["traces"])
+    got = {"u_T": [(j, u[j]) for j in make_golden.U_POINTS],
+           "recv": [(n, rec[n]) for n in make_golden.LEVELS],
+           "trace_left": [(n, tr[0, 0, n]) for n in make_golden.LEVELS],
+           "trace_right": [(n, tr[0, 1, n]) for n in make_golden.LEVELS]}
+    for key, rows in got.items():
+        assert [(i, float(v)) for i, v in rows] == stored[key], key
