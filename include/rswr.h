@@ -85,8 +85,12 @@ typedef enum rswr_mode {
     RSWR_MODE_PER_SPAN = 1    /* one launch per span (the span loop of Sec. 2.6 on the host) */
 } rswr_mode;
 
+/* The name of a status code ("RSWR_OK", ...); a static string. */
 const char* rswr_status_string(rswr_status s);
+/* A description of the last error this thread's calls returned (static
+ * storage, valid until the thread's next failing call; "" when none). */
 const char* rswr_last_error_message(void);
+/* Library version, major * 100 + minor. */
 int32_t rswr_version(void);
 
 /* ------------------------------------------------------------------------ */
@@ -123,6 +127,9 @@ typedef struct rswr_plan_info {
     int64_t workspace_bytes;
 } rswr_plan_info;
 
+/* Fills *info (host struct): the problem, its coefficients (Sec. 2.1 on the
+ * grid, both precisions), the span S and the CTA tiling of the current
+ * variant.  Errors: EINVAL for NULL arguments. */
 rswr_status rswr_plan_get_info(rswr_plan_t plan, rswr_plan_info* info);
 
 /* Steps per span, 1 <= S <= floor(overlap/2) (else EOVERLAP). */
@@ -288,6 +295,9 @@ void rswr_batch_destroy(rswr_batch_t batch);
 
 /* Writes the nprob+1 packed offsets (host array). */
 rswr_status rswr_batch_offsets(rswr_batch_t batch, int64_t* offsets);
+/* The rswr_plan_* setters and queries of the same names, for a batch (info
+ * describes problem 0 and the batch's shared tiling: span, variant, mode,
+ * total tiles and workspace). */
 rswr_status rswr_batch_get_info(rswr_batch_t batch, rswr_plan_info* info);
 rswr_status rswr_batch_set_mode(rswr_batch_t batch, int32_t mode);
 rswr_status rswr_batch_set_variant(rswr_batch_t batch, int32_t variant);
