@@ -135,7 +135,8 @@ static void window_solve(int form, int64_t nx, double c2, double k, double dx,
  *   update: every window is solved again over the selected span with its
  *       input flux set to the neighbour's predicted output flux (Sec. 2.5);
  *   combine: u = p_i on Omega_i minus the windows left of it (Sec. 2.5);
- *   redo: the next predictive span is ceil((1 + beta) Delta T_max) (Sec. 2.6).
+ *   redo: the next predictive span is ceil((1 + beta) Delta T_max) (Sec. 2.6),
+ *       with beta taken in thousandths so that the product is exact.
  * spans[m] receives the m-th selected span; *nspans their number.
  * Returns 0 on success.
  */
@@ -150,8 +151,11 @@ int oracle_rswr_paper(int form, int64_t nx, int64_t T, double c, double c2, doub
     int64_t cap = (int64_t)ceil(cap_real) - 1;
     if (cap < 1) cap = 1;
     int64_t tau = tau0 > 0 ? tau0 : ov;
+    /* beta in thousandths: the next predictive span ceil((1 + beta) span) is
+     * then exact integer arithmetic (in doubles, 1.1 * 50 rounds above 55) */
+    int64_t beta_m = (int64_t)llround(beta * 1000.0);
     int64_t tau_max = tau > cap ? tau : cap;
-    tau_max = (int64_t)ceil((1.0 + beta) * (double)tau_max) + 1;
+    tau_max = (tau_max * (1000 + beta_m) + 999) / 1000 + 1;
 
     double* u = (double*)calloc(nx, sizeof(double));
     double* w = (double*)calloc(nx, sizeof(double));
@@ -221,7 +225,7 @@ int oracle_rswr_paper(int form, int64_t nx, int64_t T, double c, double c2, doub
         if (spans) spans[m] = span;
         ++m;
         n0 += span;
-        tau = (int64_t)ceil((1.0 + beta) * (double)span);
+        tau = (span * (1000 + beta_m) + 999) / 1000;
         if (tau > tau_max) tau = tau_max;
     }
     if (nspans) *nspans = m;

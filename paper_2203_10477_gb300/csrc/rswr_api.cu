@@ -1471,7 +1471,9 @@ rswr_status run_paper(Engine* e, const Real* fA, const Real* fB, int64_t T, cons
     int64_t cap = (int64_t)std::ceil((double)(ov - 1) / (2.0 * ph.c)) - 1;
     if (cap < 1) cap = 1;
     int64_t tau = ov;
-    const int64_t tau_max = (int64_t)std::ceil((1.0 + beta) * (double)std::max(tau, cap)) + 1;
+    // beta in thousandths: ceil((1 + beta) span) in exact integer arithmetic
+    const int64_t beta_m = (int64_t)std::llround(beta * 1000.0);
+    const int64_t tau_max = (std::max(tau, cap) * (1000 + beta_m) + 999) / 1000 + 1;
     auto wl = [&](int64_t i) { return std::max<int64_t>(i * nx / N - el, 0); };
     auto wr = [&](int64_t i) { return std::min<int64_t>((i + 1) * nx / N - 1 + er, nx - 1); };
     // re-solve tiles: each subdomain's part of the combined solution, in chunks
@@ -1574,7 +1576,7 @@ rswr_status run_paper(Engine* e, const Real* fA, const Real* fB, int64_t T, cons
         n0 += span;
         std::swap(X0, Y0);
         std::swap(X1, Y1);
-        tau = (int64_t)std::ceil((1.0 + beta) * (double)span);
+        tau = ((int64_t)span * (1000 + beta_m) + 999) / 1000;
         if (tau > tau_max) tau = tau_max;
     }
     if (nspans) *nspans = m_count;

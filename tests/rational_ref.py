@@ -103,3 +103,116 @@ def tangent_dc2(nx, T, c2, fA, fB, jr, wbar):
         dprev, du = du, dnew
         total += wbar[n + 1] * du[jr]
     return total
+
+
+def _ceil_frac(q):
+    """Smallest integer >= the rational q."""
+    q = Fraction(q)
+    return -((-q.numerator) // q.denominator)
+
+
+def rswr_paper(nx, T, c, c2, k, dx, fA, fB, N, ov, tau0=None, beta=Fraction(1, 10), record=None):
+    """The paper's own RSWR loop in exact arithmetic (Sec. 2.3-2.6, Sec. 3).
+
+    Each span starts from the combined (true) state pair at level n0:
+      predict  every window is advanced over the predictive span with a zero
+               input flux at each interior end (mirror ghost);
+      select   at an overlap point x of windows i and i+1 the point span is the
+               number of leading levels n0+1, n0+2, ... at which the two
+               predictions are equal; a pair's span is the largest point span
+               of its overlap, the global span the smallest pair span, bounded
+               by the Waveform Time Span Theorem (largest whole number of
+               steps below (ov - 1)/(2c), i.e. below Delta X_overlap / (2a))
+               and by the predictive span itself, and at least one step;
+      update   every window is solved again over the selected span, an input
+               end taking the neighbour's predicted output flux
+               g = (p[e+1] - p[e-1]) / (2 dx) as Neumann data
+               (ghost = inner value -/+ 2 dx g);
+      combine  a point takes the value of the leftmost window that holds it;
+      redo     the next predictive span is ceil((1 + beta) * span) (beta = 0.1,
+               Sec. 2.6), limited to ceil((1 + beta) max(tau0, cap)) + 1.
+    c, c2, k, dx are the scheme's coefficients (rationals, or floats taken at
+    their exact binary value).  Returns (u^T, u^{T-1}, spans).  When `record`
+    is a list, (n0, steps, [span of each pair]) is appended for every span."""
+    c, c2, k, dx = Fraction(c), Fraction(c2), Fraction(k), Fraction(dx)
+    el, er = (ov + 1) // 2, ov // 2
+    win = []
+    for i in range(N):
+        b0, b1 = i * nx // N, (i + 1) * nx // N
+        win.append((max(b0 - el, 0), min(b1 - 1 + er, nx - 1)))
+    cap = max(_ceil_frac(Fraction(ov - 1) / (2 * c)) - 1, 1)
+    tau = tau0 if tau0 else ov
+    tau_lim = _ceil_frac((1 + beta) * max(tau, cap)) + 1
+
+    u = [Fraction(0)] * nx
+    u[0], u[-1] = Fraction(fA[0]), Fraction(fB[0])
+    prev = list(u)
+
+    def solve(L, R, n0, steps, flux_left=None, flux_right=None):
+        """Levels n0..n0+steps of window [L, R] as dicts j -> value; an
+        interior end takes the ghost from the given flux per level (zero flux
+        when None)."""
+        cur = {j: u[j] for j in range(L, R + 1)}
+        old = {j: prev[j] for j in range(L, R + 1)}
+        levels = [cur]
+        for s in range(steps):
+            n = n0 + s
+            new = {}
+            for j in range(L, R + 1):
+                if j == 0:
+                    new[j] = Fraction(fA[n + 1])
+                    continue
+                if j == nx - 1:
+                    new[j] = Fraction(fB[n + 1])
+                    continue
+                if j == L:
+                    g = flux_left[s] if flux_left is not None else 0
+                    west = cur[j + 1] - 2 * dx * g
+                else:
+                    west = cur[j - 1]
+                if j == R:
+                    g = flux_right[s] if flux_right is not None else 0
+                    east = cur[j - 1] + 2 * dx * g
+                else:
+                    east = cur[j + 1]
+                new[j] = c2 * (west + east) + k * cur[j] - old[j]
+            old, cur = cur, new
+            levels.append(cur)
+        return levels
+
+    spans = []
+    n0 = 0
+    while n0 < T:
+        steps = min(tau, T - n0)
+        pred = [solve(L, R, n0, steps) for (L, R) in win]
+        pairs = []
+        for i in range(N - 1):
+            lo, hi = win[i + 1][0], win[i][1]  # the overlap of windows i and i+1
+            pair = 0
+            for x in range(lo, hi + 1):
+                s = 1
+                while s <= steps and pred[i][s][x] == pred[i + 1][s][x]:
+                    s += 1
+                pair = max(pair, s - 1)
+            pairs.append(pair)
+        if record is not None:
+            record.append((n0, steps, pairs))
+        span = max(1, min([steps, cap] + pairs))
+        nu, nprev = [None] * nx, [None] * nx
+        for i, (L, R) in enumerate(win):
+            fl = fr = None
+            if i > 0 and L > 0:
+                p = pred[i - 1]
+                fl = [(p[s][L + 1] - p[s][L - 1]) / (2 * dx) for s in range(span)]
+            if i < N - 1 and R < nx - 1:
+                p = pred[i + 1]
+                fr = [(p[s][R + 1] - p[s][R - 1]) / (2 * dx) for s in range(span)]
+            lv = solve(L, R, n0, span, fl, fr)
+            for j in range(L, R + 1):
+                if nu[j] is None:
+                    nu[j], nprev[j] = lv[span][j], lv[span - 1][j]
+        u, prev = nu, nprev
+        spans.append(span)
+        n0 += span
+        tau = min(_ceil_frac((1 + beta) * span), tau_lim)
+    return u, prev, spans

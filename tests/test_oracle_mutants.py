@@ -10,6 +10,7 @@ oracle (all must pass) and against every mutant (at least one must fail).
 from __future__ import annotations
 
 import ctypes
+import functools
 import os
 import shutil
 import subprocess
@@ -25,7 +26,7 @@ from tests import rational_ref as rr
 
 SRC = os.path.dirname(os.path.abspath(oracle.__file__))
 
-# (file, original text, planted mistake)
+# (file, original text, planted mistake), or (file, [(original, mistake), ...])
 MUTANTS = {
     "canonical: sign of the centre term": ("leapfrog_body.h", "*u_new = FMA(c2, s, t);", "*u_new = FMA(c2, s, -t);"),
     "canonical: previous level added": ("leapfrog_body.h", "REAL t = FMA(k, uC, -w);", "REAL t = FMA(k, uC, w);"),
@@ -69,6 +70,22 @@ MUTANTS = {
     "source: only in the window's core": ("leapfrog_body.h",
                                           "if (src && nsrc > 0) NAME(add_sources)(form, nx, T, n, nsrc, src_j, src, L, R, pu, qu, qw);",
                                           "if (src && nsrc > 0) NAME(add_sources)(form, nx, T, n, nsrc, src_j, src, b0, b1 - 1, pu, qu, qw);"),
+    # the paper-literal select (Sec. 2.4, Sec. 3) and predictive span (Sec. 2.6)
+    "paper-literal: agreement ignored": ("rswr_oracle.c", "if (agree > best) best = agree;", "best = steps;"),
+    "paper-literal: minimum over the overlap": ("rswr_oracle.c", [("int64_t best = 0;", "int64_t best = steps;"),
+                                                                  ("if (agree > best) best = agree;",
+                                                                   "if (agree < best) best = agree;")]),
+    "paper-literal: maximum over the pairs": ("rswr_oracle.c", [("int64_t span = steps;", "int64_t span = 0;"),
+                                                                ("if (best < span) span = best;",
+                                                                 "if (best > span) span = best;")]),
+    "paper-literal: agreement from level 0": ("rswr_oracle.c",
+                                              "p1[(agree + 1) * nx + x] == p2[(agree + 1) * nx + x]",
+                                              "p1[agree * nx + x] == p2[agree * nx + x]"),
+    "paper-literal: beta dropped": ("rswr_oracle.c", "tau = (span * (1000 + beta_m) + 999) / 1000;", "tau = span;"),
+    "paper-literal: beta product in floating point": ("rswr_oracle.c", "tau = (span * (1000 + beta_m) + 999) / 1000;",
+                                                      "tau = (int64_t)ceil((1.0 + beta) * (double)span);"),
+    "paper-literal: theorem cap one step longer": ("rswr_oracle.c", "int64_t cap = (int64_t)ceil(cap_real) - 1;",
+                                                   "int64_t cap = (int64_t)ceil(cap_real);"),
 }
 
 
@@ -78,11 +95,17 @@ def build_variant(tmp, name, mutation):
     for f in ("rswr_oracle.c", "leapfrog_body.h"):
         shutil.copy(os.path.join(SRC, f), d)
     if mutation is not None:
-        f, old, new = mutation
+        f, edits = mutation[0], mutation[1:]
+        if len(edits) == 2:  # one (old, new) replacement
+            edits = [tuple(edits)]
+        else:  # a list of them
+            edits = edits[0]
         p = os.path.join(d, f)
         text = open(p).read()
-        assert text.count(old) >= 1, f"mutation anchor not found: {old}"
-        open(p, "w").write(text.replace(old, new, 1))
+        for old, new in edits:
+            assert text.count(old) >= 1, f"mutation anchor not found: {old}"
+            text = text.replace(old, new, 1)
+        open(p, "w").write(text)
     lib = os.path.join(d, "lib.so")
     subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", lib,
                     os.path.join(d, "rswr_oracle.c"), "-lm"], check=True, cwd=d)
@@ -230,7 +253,31 @@ def chk_sources():
     return bool(ok)
 
 
-CHECKS = {"sources": chk_sources, "dalembert": chk_dalembert, "mode": chk_mode, "rational-canonical": lambda: chk_rational(0),
+@functools.lru_cache(maxsize=None)
+def _paper_select_expect(nx, N, ov, cfl, T, delay, tau0):
+    """Spans of the exact-rational restatement of the paper's loop."""
+    dt = cfl / (nx - 1)
+    cf = oracle.coeffs(0.0, 1.0, 1.0, nx, dt)
+    m = np.arange(T + 1) - delay
+    fA = np.where((m > 0) & (m < 8), np.round(np.sin(np.pi * m / 8) ** 2 * 64) / 64, 0.0)
+    return fA, rr.rswr_paper(nx, T, cf.c, cf.c2, cf.k, cf.dx, fA, np.zeros(T + 1), N, ov, tau0=tau0 or None)[2]
+
+
+def chk_paper_select():
+    """The paper-literal span sequence equals the exact-rational restatement
+    (select below the cap, several pairs, beta growth, exact beta rounding)."""
+    ok = True
+    for case in [(33, 2, 8, 0.5, 60, 0, 0), (41, 3, 10, 0.6, 80, 0, 0), (41, 4, 8, 0.5, 60, 25, 2)]:
+        nx, N, ov, cfl, T, delay, tau0 = case
+        fA, spans = _paper_select_expect(*case)
+        got = oracle.rswr_paper(nx, T, 1.0, cfl / (nx - 1), fA, np.zeros(T + 1), N, ov, tau0=tau0)
+        ok &= list(got["spans"]) == spans
+    z = np.zeros(164)
+    ok &= list(oracle.rswr_paper(121, 163, 1.0, 0.5 / 120, z, z, 2, 60, tau0=50)["spans"]) == [50, 55, 58]
+    return bool(ok)
+
+
+CHECKS = {"paper-select": chk_paper_select, "sources": chk_sources, "dalembert": chk_dalembert, "mode": chk_mode, "rational-canonical": lambda: chk_rational(0),
           "rational-increment": lambda: chk_rational(1), "energy": chk_energy, "rswr": chk_rswr,
           "paper": chk_paper, "adjoint": chk_adjoint}
 

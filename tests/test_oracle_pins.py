@@ -331,6 +331,126 @@ def test_rswr_paper_literal_matches_monolithic(oracle_mod, N, ov, cfl):
 
 
 # ----------------------------------------------------------------------------
+# the paper-literal select and the beta rule (Sec. 2.4, Sec. 3, Sec. 2.6)
+# ----------------------------------------------------------------------------
+
+def delayed_pulse(T, delay, width=8):
+    """A boundary pulse with dyadic samples (sin^2 rounded to 1/64), silent
+    for the first `delay` steps."""
+    m = np.arange(T + 1) - delay
+    return np.where((m > 0) & (m < width), np.round(np.sin(np.pi * m / width) ** 2 * 64) / 64, 0.0)
+
+
+# nx, N, ov, Courant number, T, pulse delay, first predictive span (0 = ov)
+PAPER_SELECT_CASES = {
+    "select binds below the cap": (33, 2, 8, 0.5, 60, 0, 0),
+    "far below the cap": (40, 3, 8, 0.3, 70, 0, 0),
+    "pairs differ": (41, 3, 10, 0.6, 80, 0, 0),
+    "quiet start grows by beta, then binds": (41, 4, 8, 0.5, 60, 25, 2),
+    "growth past the first pair's cap": (41, 3, 12, 0.5, 70, 20, 2),
+    "the theorem cap binds": (29, 2, 6, 0.9, 50, 0, 0),
+}
+
+
+@pytest.mark.parametrize("name", list(PAPER_SELECT_CASES))
+def test_paper_literal_select_equals_exact_restatement(oracle_mod, name):
+    """The oracle's data-chosen spans are those of an exact-rational run of
+    the paper's predict / select / update loop (tests/rational_ref.py), and
+    with those spans the paper-literal method reproduces the monolithic
+    solution exactly in rationals (Sec. 2.4: the selected span is valid)."""
+    nx, N, ov, cfl, T, delay, tau0 = PAPER_SELECT_CASES[name]
+    dt = cfl / (nx - 1)
+    fA = delayed_pulse(T, delay)
+    z = np.zeros(T + 1)
+    cf = oracle_mod.coeffs(0.0, 1.0, 1.0, nx, dt)
+    u, up, spans = rr.rswr_paper(nx, T, cf.c, cf.c2, cf.k, cf.dx, fA, z, N, ov, tau0=tau0 or None)
+    mono = rr.leapfrog(nx, T, Fraction(cf.c2), Fraction(cf.k), fA, z)
+    assert u == mono[-1] and up == mono[-2]
+    got = oracle_mod.rswr_paper(nx, T, 1.0, dt, fA, z, N, ov, tau0=tau0)
+    assert list(got["spans"]) == spans
+    ex = np.array([float(v) for v in u])
+    assert np.abs(got["u"] - ex).max() <= 1e-12 * np.abs(ex).max()
+
+
+def test_paper_select_cases_cover_binding_growth_and_cap(oracle_mod):
+    """The cases above are chosen so that each part of the select rule
+    decides some span: the agreement test below the theorem cap, the minimum
+    over several pairs, the beta growth from a small first span, the cap."""
+    seen = {"below cap": False, "grows": False, "cap": False, "pair min": False}
+    for nx, N, ov, cfl, T, delay, tau0 in PAPER_SELECT_CASES.values():
+        dt = cfl / (nx - 1)
+        cf = oracle_mod.coeffs(0.0, 1.0, 1.0, nx, dt)
+        cap = math.ceil((ov - 1) / (2 * cf.c)) - 1
+        spans = list(oracle_mod.rswr_paper(nx, T, 1.0, dt, delayed_pulse(T, delay), np.zeros(T + 1), N, ov,
+                                           tau0=tau0)["spans"])
+        full = spans[:-1]  # the last span may be cut by T
+        seen["below cap"] |= any(s < cap for s in full)
+        seen["cap"] |= cap in full
+        seen["grows"] |= any(b > a for a, b in zip(full, full[1:]))
+        rec = []
+        rr.rswr_paper(nx, T, cf.c, cf.c2, cf.k, cf.dx, delayed_pulse(T, delay), np.zeros(T + 1), N, ov,
+                      tau0=tau0 or None, record=rec)
+        # a span decided by one pair while another pair would allow more
+        seen["pair min"] |= any(min(p) < min(max(p), steps, cap) for _, steps, p in rec)
+    assert all(seen.values()), seen
+
+
+def test_paper_beta_rule_is_exact(oracle_mod):
+    """Sec. 2.6: the next predictive span is (1 + beta) times the selected one
+    (beta = 0.1), rounded up.  On a quiet grid the agreement never binds, so
+    the spans are the predictive spans under the theorem cap: from a first
+    span of 50 steps the next is ceil(55.0) = 55 (a floating-point 1.1 * 50
+    rounds above 55 and would give 56), then the cap
+    ceil((ov - 1)/(2c)) - 1 = ceil(59/1) - 1 = 58."""
+    nx, N, ov, T = 121, 2, 60, 163
+    dt = 0.5 / (nx - 1)
+    z = np.zeros(T + 1)
+    got = oracle_mod.rswr_paper(nx, T, 1.0, dt, z, z, N, ov, tau0=50)
+    assert list(got["spans"]) == [50, 55, 58]
+
+
+def test_paper_literal_cfl1_spans_from_the_cone(oracle_mod):
+    """Hand-derived span sequence at Courant number 1.
+
+    With c = 1 the leapfrog carries u^n_j = F(n - j) exactly (d'Alembert).
+    Take the ramp F(s) = s/8 for s >= 1 entering at x = 0, N = 2, ov = 16 on
+    nx = 65 (dx = 1/64: every value and flux is exact in binary), so the
+    overlap is [L, R] = [24, 39] and the theorem cap is the largest integer
+    below (ov - 1)/2, i.e. 7.  A zero-flux ghost at an interior end e first
+    differs from the truth at the level after the front reaches e (level
+    max(n0, e) + 1), and at c = 1 that error travels exactly one point per
+    step with an unchanged leading value, so at overlap point x the
+    predictions of a span starting at n0 first differ at level
+        min(max(n0, R) + 1 + (R - x), max(n0, L) + 1 + (x - L)).
+    The agreement at x is that level minus n0 + 1 (clipped to the span), the
+    span is its maximum over x, capped by 7, and the first predictive span is
+    3, so the spans grow by beta (3, 4, 5, 6, 7) and then stay at the cap.
+    The final state is d'Alembert's F(T - j), bit for bit."""
+    nx, N, ov, T, tau0 = 65, 2, 16, 60, 3
+    dt = 1.0 / (nx - 1)
+    F = lambda s: s / 8.0 if s >= 1 else 0.0
+    fA = np.array([F(n) for n in range(T + 1)])
+    z = np.zeros(T + 1)
+    L, R, cap = 24, 39, 7
+    expect, n0, tau = [], 0, tau0
+    while n0 < T:
+        steps = min(tau, T - n0)
+        best = 0
+        for x in range(L, R + 1):
+            first = min(max(n0, R) + 1 + (R - x), max(n0, L) + 1 + (x - L))
+            best = max(best, min(first - n0 - 1, steps))
+        span = max(1, min(best, steps, cap))
+        expect.append(span)
+        n0 += span
+        tau = -(-11 * span // 10)
+    assert expect[:6] == [3, 4, 5, 6, 7, 7] and sum(expect) == T
+    got = oracle_mod.rswr_paper(nx, T, 1.0, dt, fA, z, N, ov, tau0=tau0)
+    assert got["coeffs"].c == 1.0
+    assert list(got["spans"]) == expect
+    assert np.array_equal(got["u"], np.array([F(T - j) for j in range(nx)]))
+
+
+# ----------------------------------------------------------------------------
 # adjoint
 # ----------------------------------------------------------------------------
 
