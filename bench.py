@@ -43,8 +43,10 @@ METRIC = "GLUP/s and % stencil roofline, RSWR vs monolithic GPU leapfrog at FP64
 UNIT = "GLUP/s"
 WORKLOAD = "1-D wave a=1, nx=2^24, N=1024 subdomains, overlap 64, CFL 0.9, 10^4 steps, Gaussian pulse"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
+# streaming multiprocessors of the device; main() sets it from the device
+# properties before any roofline is computed
+SM_COUNT = None
 
 
 def load_peaks() -> dict:
@@ -94,13 +96,24 @@ def measured_traffic(dtype: str, variant: int, span: int):
 ADJ_OPS = {"f64": {"g": 3, "full": 3 + 3 + 1 + 1 + 3}, "f32": {"g": 4, "full": 4 + 4 + 0 + 1 + 4}}
 
 
+# FMA rates of the two pipes measured on this device by rswr_fma_probe (set in main)
+MEASURED_ALU = {}
+
+
 def alu_roofline(dtype: str, value: float, ops: int) -> dict:
     """ALU roofline of a path doing `ops` arithmetic instructions per update on the
-    FP64 pipe (2 / clock / SM) or the FP32 pipe (128 lanes / clock / SM) at 2070 MHz."""
+    FP64 pipe (2 / clock / SM) or the FP32 pipe (128 lanes / clock / SM) at 2070 MHz,
+    with the same bound from the pipe rate measured by the FMA probe beside it."""
     lanes = 2 if dtype == "f64" else 128
     peak = SM_COUNT * lanes * 2.07e9 / ops / 1e9
-    return {"bound": "alu", "unit": "GLUP/s", "peak": peak, "frac": value / peak,
-            "ops_per_update": ops, "pipe": "fp64" if dtype == "f64" else "fp32"}
+    out = {"bound": "alu", "unit": "GLUP/s", "peak": peak, "frac": value / peak,
+           "ops_per_update": ops, "pipe": "fp64" if dtype == "f64" else "fp32",
+           "peak_definition": f"{SM_COUNT} SMs x {lanes} {dtype.upper()} lanes/clk x 2070 MHz / {ops} instr per update"}
+    m = MEASURED_ALU.get(dtype)
+    if m:
+        out["peak_measured"] = m["fma_per_s"] / ops / 1e9
+        out["frac_of_measured"] = value / out["peak_measured"]
+    return out
 
 
 def span_roofline(dtype: str, value: float, ops: int, info: dict) -> dict:
@@ -118,6 +131,23 @@ def span_roofline(dtype: str, value: float, ops: int, info: dict) -> dict:
     if hbm_peak < alu["peak"]:
         out.update(bound="hbm", peak=hbm_peak, frac=value / hbm_peak)
     return out
+
+
+def measure_alu(torch, dev) -> dict:
+    """FMA throughput of the FP64 and FP32 pipes on `dev` (rswr_fma_probe),
+    with the SM clocks sampled while the probe ran."""
+    from paper_2203_10477_gb300 import rswr
+
+    clocks = ClockSampler(gpu_uuid(torch, dev))
+    clocks.start()
+    time.sleep(0.3)
+    res = {name: rswr.fma_rate(dt, device=dev) for name, dt in (("f64", rswr.F64), ("f32", rswr.F32))}
+    clk = clocks.stop()
+    mhz = clk["sm_mhz"] if clk else SM_MAX_MHZ
+    for r in res.values():
+        r["per_sm_per_clock"] = r["fma_per_s"] / (r["sms"] * mhz * 1e6)
+    res["clocks"] = clk
+    return res
 
 
 def alu_peaks(sm_mhz: float) -> dict:
@@ -210,26 +240,48 @@ class ClockSampler:
 # the reference arm and the CPU baseline: the oracle on the host cores
 # ----------------------------------------------------------------------------
 
-def oracle_sample(p, steps: int) -> float:
-    """Seconds for `steps` leapfrog steps of the CPU oracle over the full grid."""
+def host_cores() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(p, steps: int, threads: int = 1) -> float:
+    """Seconds for `steps` leapfrog steps of the CPU oracle over the full grid
+    on `threads` host threads (the result is the same bit for bit)."""
     import oracle
 
-    t0 = time.perf_counter()
-    oracle.leapfrog(p.nx, steps, p.a, p.dt, p.fA[: steps + 1], p.fB[: steps + 1])
-    return time.perf_counter() - t0
+    oracle.set_threads(threads)
+    try:
+        t0 = time.perf_counter()
+        oracle.leapfrog(p.nx, steps, p.a, p.dt, p.fA[: steps + 1], p.fB[: steps + 1])
+        return time.perf_counter() - t0
+    finally:
+        oracle.set_threads(1)
 
 
-def cpu_baseline(p, budget_s: float = 15.0) -> dict:
+def cpu_baseline(p, budget_s: float = 10.0) -> dict:
+    """The oracle's monolithic leapfrog on all host cores (the reported value)
+    and on one core, each on a sample of about `budget_s` seconds."""
     import oracle
 
     oracle.build()
-    t1 = oracle_sample(p, 2)
-    steps = int(max(2, min(p.T, budget_s / max(t1 / 2, 1e-9))))
-    secs = oracle_sample(p, steps)
-    lups = (p.nx - 2) * steps
-    return {"value": lups / secs / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 canonical oracle leapfrog (plain C, one thread), full nx=2^24 grid, {steps} of the "
-                      f"10^4 steps, {secs:.1f} s"}
+    res = {}
+    for cores in (host_cores(), 1):
+        t1 = oracle_sample(p, 2, cores)
+        steps = int(max(2, min(p.T, budget_s / max(t1 / 2, 1e-9))))
+        secs = oracle_sample(p, steps, cores)
+        res[cores] = ((p.nx - 2) * steps / secs / 1e9, steps, secs)
+    n = host_cores()
+    v, steps, secs = res[n]
+    v1, steps1, secs1 = res[1]
+    return {"value": v, "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": f"FP64 canonical oracle leapfrog (plain C, OpenMP over the points of a level, {n} threads), "
+                      f"full nx=2^24 grid, {steps} of the 10^4 steps, {secs:.1f} s",
+            "single_core": {"value": v1, "unit": UNIT, "cores": 1,
+                            "sample": f"the same on one thread, {steps1} steps, {secs1:.1f} s"}}
 
 
 def run_reference(args, rank: int, world: int) -> None:
@@ -239,11 +291,12 @@ def run_reference(args, rank: int, world: int) -> None:
     import oracle
 
     oracle.build()
-    t1 = oracle_sample(p, 2)
+    cores = host_cores()
+    t1 = oracle_sample(p, 2, cores)
     steps_per = int(max(2, min(p.T, 4.0 / max(t1 / 2, 1e-9))))  # about 4 s of CPU work per step
     for _ in range(args.warmup):
-        oracle_sample(p, steps_per)
-    times = [oracle_sample(p, steps_per) for _ in range(args.steps)]
+        oracle_sample(p, steps_per, cores)
+    times = [oracle_sample(p, steps_per, cores) for _ in range(args.steps)]
     total = sum(times)
     lups = (p.nx - 2) * steps_per * args.steps
     value = lups / total / 1e9
@@ -253,12 +306,123 @@ def run_reference(args, rank: int, world: int) -> None:
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": {"workload": WORKLOAD, "nx": p.nx, "n_sub": p.n_sub, "overlap": p.overlap, "cfl": 0.9,
                    "T": p.T, "sample_steps_per_step": steps_per},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"each step: FP64 oracle leapfrog over the full nx=2^24 grid for {steps_per} "
-                                   f"of the 10^4 time steps"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: FP64 oracle leapfrog (OpenMP, {cores} threads) over the full "
+                                   f"nx=2^24 grid for {steps_per} of the 10^4 time steps"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# the checker leg: FP32 results against the FP64 oracle (outside timed regions)
+# ----------------------------------------------------------------------------
+
+def host_map(fn, items):
+    """fn over items on the host cores (the oracle's C calls release the GIL)."""
+    import concurrent.futures as cf
+
+    import oracle
+
+    oracle.build()
+    oracle.set_threads(1)
+    with cf.ThreadPoolExecutor(max_workers=host_cores()) as ex:
+        return list(ex.map(fn, items))
+
+
+def rel_max(u, ref) -> float:
+    """max |u - ref| / max |ref| in FP64."""
+    u = np.asarray(u, np.float64)
+    ref = np.asarray(ref, np.float64)
+    scale = float(np.abs(ref).max())
+    return float(np.abs(u - ref).max()) / scale if scale > 0 else float(np.abs(u).max())
+
+
+def prefix_ref(p, T=None):
+    """The FP64 oracle on the causal prefix of a zero-data run with a quiet
+    right end: level T vanishes beyond j = T + 1, so the grid truncated to
+    T + 2 points gives the full grid's values there."""
+    import oracle
+
+    T = p.T if T is None else T
+    m = oracle.causal_extent(T, p.nx)
+    return m, oracle.leapfrog(p.nx, T, p.a, p.dt, p.fA[: T + 1], p.fB[: T + 1], nx_run=m)["u"]
+
+
+def state_error(u_dev, p) -> dict:
+    """FP32 final state (device) of one problem against the FP64 oracle on its
+    causal prefix; the FP32 state beyond the prefix must be exactly 0."""
+    m, ref = prefix_ref(p)
+    u = u_dev[:m].double().cpu().numpy()
+    tail = int((u_dev[m:] != 0).sum()) if m < p.nx else 0
+    return {"err_vs_fp64": rel_max(u, ref), "prefix_points": m, "nonzero_beyond_prefix": tail}
+
+
+def batch_state_error(out_dev, offsets, probs, idx=None) -> dict:
+    """state_error over the problems `idx` (all by default) of a packed batch output."""
+    idx = list(range(len(probs))) if idx is None else list(idx)
+    refs = host_map(lambda i: prefix_ref(probs[i]), idx)
+    errs, tail = [], 0
+    for i, (m, ref) in zip(idx, refs):
+        o0, o1 = int(offsets[i]), int(offsets[i + 1])
+        u = out_dev[o0:o0 + m].double().cpu().numpy()
+        errs.append(rel_max(u, ref))
+        if o0 + m < o1:
+            tail += int((out_dev[o0 + m:o1] != 0).sum())
+    return {"err_vs_fp64": max(errs), "err_vs_fp64_median": float(np.median(errs)), "problems_checked": len(idx),
+            "problems_above_1e-5": int(sum(e > 1e-5 for e in errs)), "nonzero_beyond_prefix": tail}
+
+
+def pulse10_error(u_dev, p, j, s) -> dict:
+    """FP32 final state of the pulse-source run against the FP64 oracle.  Each
+    source's disturbance stays within T points of it (zero data and quiet
+    ends), and the sources are far apart, so the oracle runs each source on the
+    2T + 5 points around it (same coefficients, zero ends); every other point
+    must be exactly 0."""
+    import oracle
+
+    T = p.T
+    m = 2 * T + 5
+    z = np.zeros(T + 1)
+
+    def one(q):
+        lo = int(j[q]) - T - 2
+        assert lo >= 1 and lo + m <= p.nx - 1
+        return lo, oracle.leapfrog(p.nx, T, p.a, p.dt, z, z, nx_run=m, src_j=[T + 2], src=s[q:q + 1])["u"]
+
+    refs = host_map(one, range(len(j)))
+    covered = np.zeros(p.nx, bool)
+    err_num, scale = 0.0, 0.0
+    for lo, ref in refs:
+        u = u_dev[lo:lo + m].double().cpu().numpy()
+        err_num = max(err_num, float(np.abs(u - ref).max()))
+        scale = max(scale, float(np.abs(ref).max()))
+        covered[lo:lo + m] = True
+    mask = torch_from_numpy_like(covered, u_dev)
+    tail = int((u_dev[~mask] != 0).sum())
+    return {"err_vs_fp64": err_num / scale, "nonzero_outside_cones": tail, "sources_checked": len(refs)}
+
+
+def torch_from_numpy_like(a, like):
+    import torch
+
+    return torch.from_numpy(a).to(like.device)
+
+
+def grad_error(g32, ga32, p, j_r, wbar, want_a=True, nx_run=None) -> dict:
+    """FP32 gradients against the FP64 oracle's discrete adjoint (same inputs
+    in FP64): relative 2-norm error of dL/dfA, relative error of dL/da."""
+    import oracle
+
+    m = nx_run or oracle.causal_extent(p.T, p.nx)
+    ref = oracle.adjoint(p.nx, p.T, p.a, p.dt, p.fA, p.fB, j_r, np.asarray(wbar, np.float64), nx_run=m)
+    g = np.asarray(g32, np.float64)
+    out = {"grad_fA_err_vs_fp64": float(np.linalg.norm(g - ref["dg"]) / np.linalg.norm(ref["dg"]))}
+    if want_a:
+        out["grad_a_err_vs_fp64"] = abs(float(ga32) - ref["da"]) / abs(ref["da"])
+        out["grad_a_err_vs_fp64_of_sum_abs_terms"] = abs(float(ga32) - ref["da"]) / ref["abs_da"]
+    out["_ref"] = ref
+    return out
 
 
 # ----------------------------------------------------------------------------
@@ -468,11 +632,15 @@ def bench_batched(torch, rank, world, dist, dev):
     t = max_over_ranks([sum(ms) / len(ms) / 1e3], dist, dev)[0]
     tot = sum_over_ranks([lups], dist, dev)[0]
     info = b.info()
+    # checker leg: every problem of this rank against the FP64 oracle on its causal prefix
+    err = batch_state_error(out[0], b.offsets, mine)
     return {"workload": "4096 problems, nx U[2^10,2^18], a U[0.5,2], CFL 0.8, 4096 steps, overlap 32, FP32",
             "value": tot / t / 1e9, "unit": UNIT, "ms_per_run": 1e3 * t, "lups_per_run": tot,
             "variant": info["variant"], "span_steps": info["span_steps"], "mode": info["mode"],
             "sharding": f"{world} rank(s), whole problems per rank",
-            "roofline": span_roofline("f32", tot / t / 1e9 / world, 4, info)}
+            "roofline": span_roofline("f32", tot / t / 1e9 / world, 4, info),
+            "error_vs_fp64_oracle": dict(err, note="max over every problem of this rank, causal prefix "
+                                                    "j <= T + 1 (or the whole grid when shorter)")}
 
 
 def bench_adjoint(torch, dev):
@@ -490,7 +658,11 @@ def bench_adjoint(torch, dev):
         td = torch.float64 if dtype == rswr.F64 else torch.float32
         fA = torch.as_tensor(p.fA, device=dev).to(td)
         wt = w.to(td)
-        full = lambda: plan.adjoint(fA, None, p.T, 4000, wt, want_a=True)
+        last = {}
+
+        def full():
+            last["r"] = plan.adjoint(fA, None, p.T, 4000, wt, want_a=True)
+
         gonly = lambda: plan.adjoint(fA, None, p.T, 4000, wt, want_a=False)
         full()
         gonly()
@@ -504,6 +676,15 @@ def bench_adjoint(torch, dev):
                                        "roofline": alu_roofline(name, v_full, ADJ_OPS[name]["full"])},
                      "grad_fA_only": {"value": v_g, "ms": min(ms_g),
                                       "roofline": alu_roofline(name, v_g, ADJ_OPS[name]["g"])}}
+        # checker leg: the gradients of the last timed run against the FP64 oracle's adjoint
+        g = last["r"]["grad_fA"].double().cpu().numpy()
+        ga = float(last["r"]["grad_a"][0])
+        chk = grad_error(g, ga, p, 4000, inputs.lowpass_noise(p.T, seed=4))
+        ref = chk.pop("_ref")
+        if name == "f64":
+            chk = {"grad_fA_bitwise_equal_to_oracle": bool(np.array_equal(g, ref["dg"])),
+                   "grad_a_err_of_sum_abs_terms": chk["grad_a_err_vs_fp64_of_sum_abs_terms"]}
+        res[name]["check"] = chk
         res[name]["variant"] = plan.info()["variant"]
         res[name]["mode"] = plan.info()["mode"]
         res[name]["span_steps"] = plan.info()["span_steps"]
@@ -527,11 +708,13 @@ def bench_large(torch, dev):
     plan.check()
     lups = (p.nx - 2) * p.T
     info = plan.info()
+    err = state_error(out[0], p)  # checker leg, outside the timed region
     del out
     v = lups / (ms[0] / 1e3) / 1e9
     return {"workload": "c5: nx=2^28 FP32, N=8192, overlap 64, 2^15 steps", "value": v,
             "unit": UNIT, "ms_per_run": ms[0], "variant": info["variant"], "span_steps": info["span_steps"],
-            "roofline": span_roofline("f32", v, 4, info)}
+            "roofline": span_roofline("f32", v, 4, info),
+            "error_vs_fp64_oracle": dict(err, note="causal prefix j <= T + 1")}
 
 
 def bench_c5_batch(torch, rank, world, dist, dev):
@@ -556,8 +739,13 @@ def bench_c5_batch(torch, rank, world, dist, dev):
     ms_f = _time(torch, run, 1)[0]
     b.check()
     jr = [q.meta["j_r"] for q in mine]
-    wbar = torch.as_tensor(np.stack([inputs.lowpass_noise(T, seed=1000 + i) for i in idx]), device=dev).to(torch.float32)
-    adj = lambda: b.adjoint(fA, None, T, jr, wbar)
+    w64 = [inputs.lowpass_noise(T, seed=1000 + i) for i in idx]
+    wbar = torch.as_tensor(np.stack(w64), device=dev).to(torch.float32)
+    last = {}
+
+    def adj():
+        last["r"] = b.adjoint(fA, None, T, jr, wbar)
+
     adj()
     ms_a = _time(torch, adj, 1)[0]
     b.check()
@@ -565,13 +753,25 @@ def bench_c5_batch(torch, rank, world, dist, dev):
     lups = float(sum((q.nx - 2) * T for q in mine))
     t_f, t_a = max_over_ranks([ms_f / 1e3, ms_a / 1e3], dist, dev)
     tot = sum_over_ranks([lups], dist, dev)[0]
-    del out, wbar
+    # checker leg: a spread sample of the problems (by size) against the FP64 oracle
+    order = sorted(range(len(mine)), key=lambda i: mine[i].nx)
+    fwd_idx = [order[k] for k in np.linspace(0, len(order) - 1, min(16, len(order))).round().astype(int)]
+    err_f = batch_state_error(out[0], b.offsets, mine, sorted(set(fwd_idx)))
+    adj_idx = sorted(set(order[k] for k in np.linspace(0, len(order) - 1, min(4, len(order))).round().astype(int)))
+    g = last["r"]["grad_fA"]
+    errs = host_map(lambda i: grad_error(g[i].double().cpu().numpy(), None, mine[i], jr[i], w64[i],
+                                         want_a=False)["grad_fA_err_vs_fp64"], adj_idx)
+    del out, wbar, last
     return {"workload": "c5: 512 uneven problems, nx U[2^12,2^20], a U[0.5,2], CFL 0.9, overlap 64, 2^15 steps, FP32",
             "unit": UNIT, "lups_per_run": tot,
             "forward": {"value": tot / t_f / 1e9, "ms_per_run": t_f * 1e3,
-                        "roofline": span_roofline("f32", tot / t_f / 1e9, 4, info)},
+                        "roofline": span_roofline("f32", tot / t_f / 1e9, 4, info),
+                        "error_vs_fp64_oracle": dict(err_f, note="16 problems spread over the sizes, causal prefix")},
             "adjoint_grad_fA": {"value": tot / t_a / 1e9, "ms_per_run": t_a * 1e3,
-                                "roofline": span_roofline("f32", tot / t_a / 1e9, 4, info)},
+                                "roofline": span_roofline("f32", tot / t_a / 1e9, 4, info),
+                                "error_vs_fp64_oracle": {"grad_fA_err_vs_fp64": max(errs),
+                                                         "per_problem": errs, "problems_checked": len(adj_idx),
+                                                         "norm": "relative 2-norm"}},
             "variant": info["variant"], "span_steps": info["span_steps"], "mode": info["mode"],
             "sharding": f"{world} rank(s), whole problems per rank"}
 
@@ -594,6 +794,12 @@ def bench_paper_literal(torch, dev, T=2000):
         secs = time.perf_counter() - t0
         res[name] = {"value": (p.nx - 2) * p.T / secs / 1e9, "seconds": secs, "spans": int(len(r["spans"])),
                      "mean_span": float(np.mean(r["spans"]))}
+        m, ref = prefix_ref(p)
+        u = out[0][:m].double().cpu().numpy()
+        if name == "f64":
+            res[name]["err_vs_monolithic_oracle"] = rel_max(u, ref)
+        else:
+            res[name]["error_vs_fp64_oracle"] = {"err_vs_fp64": rel_max(u, ref), "note": "causal prefix"}
     return res
 
 
@@ -630,6 +836,8 @@ def bench_pulse10(torch, dev, T=10_000):
                                                                                    and torch.equal(out[1], ref[1])),
                      "max_abs_u": float(out[0].abs().max()), "variant": info["variant"],
                      "span_steps": info["span_steps"], "roofline": span_roofline(name, v, ops, info)}
+        if name == "f32":
+            res[name]["error_vs_fp64_oracle"] = pulse10_error(out[0], p, j, s)
         del out, ref
     return res
 
@@ -652,6 +860,8 @@ def main():
                          "adj64/adj32: default 20 = the c4 grid)")
     ap.add_argument("--span", type=int, default=None, help="steps per span of the profiling case")
     ap.add_argument("--full", action="store_true", help="profiling case at the bench's full size")
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure the FP64 / FP32 pipe rates with the library's FMA probe kernel and exit")
     args = ap.parse_args()
 
     if args.profile_case:
@@ -671,8 +881,23 @@ def main():
 
     import torch
 
+    global SM_COUNT
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    SM_COUNT = torch.cuda.get_device_properties(dev).multi_processor_count
+    if args.peaks:
+        from paper_2203_10477_gb300 import build
+
+        build.build()
+        m = measure_alu(torch, dev)
+        print(json.dumps({"peaks": "FMA throughput of the FP64 and FP32 pipes (rswr_fma_probe)", "sms": SM_COUNT,
+                          "f64_fma_per_s": m["f64"]["fma_per_s"], "f32_fma_per_s": m["f32"]["fma_per_s"],
+                          "f64_per_sm_per_clock": m["f64"]["per_sm_per_clock"],
+                          "f32_per_sm_per_clock": m["f32"]["per_sm_per_clock"],
+                          "f64_glups_at_3_instr": m["f64"]["fma_per_s"] / 3 / 1e9,
+                          "f32_glups_at_4_instr": m["f32"]["fma_per_s"] / 4 / 1e9,
+                          "detail": m}), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist_
@@ -683,6 +908,8 @@ def main():
     from paper_2203_10477_gb300 import build, rswr
 
     build.build()
+    alu_measured = measure_alu(torch, dev)
+    MEASURED_ALU.update({k: alu_measured[k] for k in ("f64", "f32")})
     p = inputs.c2()
     lups = (p.nx - 2) * p.T
     peaks = load_peaks()
@@ -710,6 +937,14 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
+
+    # checker leg (outside the timed region): the last timed runs against the
+    # FP64 oracle on the causal prefix j <= T + 1
+    m_pre, ref_pre = prefix_ref(p)
+    u64 = b64.out[0][:m_pre].cpu().numpy()
+    check64 = {"bitwise_equal_to_oracle": bool(np.array_equal(u64, ref_pre)),
+               "nonzero_beyond_prefix": int((b64.out[0][m_pre:] != 0).sum()), "prefix_points": m_pre}
+    err32 = state_error(b32.out[0], p)
 
     from paper_2203_10477_gb300.shard import max_over_ranks
 
@@ -776,10 +1011,15 @@ def main():
                      "traffic_source": "profiles/traffic_span_kernel_c2.md (bytes/update x updates per launch)",
                      "algorithmic_bytes_per_lup": bpl(8, info64["span_steps"]),
                      "achieved_gbs": k64 * bpl(8, info64["span_steps"]),
-                     "peak_definition": "152 SMs x 2 FP64 instr/clk x 2070 MHz / 3 FP64 instr per LUP"},
+                     "peak_definition": f"{SM_COUNT} SMs x 2 FP64 instr/clk x 2070 MHz / 3 FP64 instr per LUP",
+                     "peak_measured": alu_measured["f64"]["fma_per_s"] / 3 / 1e9,
+                     "frac_of_measured": k64 / (alu_measured["f64"]["fma_per_s"] / 3 / 1e9),
+                     "peak_measured_definition": "rswr_fma_probe FP64 FMA/s / 3 FP64 instr per LUP"},
+        "check_vs_oracle": check64,
         "f32": {"value": value32, "unit": UNIT, "ms_per_step": 1e3 * t32 / args.steps, "form": "increment",
                 "pct_stencil_roofline": 100.0 * value32 / n / r_hbm["f32"],
-                "error_vs_fp64_oracle": "<= 1e-5 relative (tests/test_gpu_parity.py)",
+                "error_vs_fp64_oracle": dict(err32, note="max |u32 - u64| / max |u64| of the last timed run "
+                                                         "on the causal prefix j <= T + 1"),
                 "roofline": {"bound": "alu", "kernel": "span_kernel<float, increment>", "achieved": k32,
                              "peak": alu_max["f32"], "unit": "GLUP/s", "frac": k32 / alu_max["f32"],
                              "frac_at_run_clock": k32 / alu_run["f32"],
@@ -787,7 +1027,11 @@ def main():
                                  measured_traffic("f32", info32["variant"], info32["span_steps"])),
                              "algorithmic_bytes_per_lup": bpl(4, info32["span_steps"]),
                              "achieved_gbs": k32 * bpl(4, info32["span_steps"]),
-                             "peak_definition": "152 SMs x 128 FP32 lanes x 2070 MHz / 4 FP32 instr per LUP"}},
+                             "peak_definition": f"{SM_COUNT} SMs x 128 FP32 lanes x 2070 MHz / 4 FP32 instr per LUP",
+                             "peak_measured": alu_measured["f32"]["fma_per_s"] / 4 / 1e9,
+                             "frac_of_measured": k32 / (alu_measured["f32"]["fma_per_s"] / 4 / 1e9)}},
+        "alu_measured": {k: {kk: alu_measured[k][kk] for kk in ("fma_per_s", "per_sm_per_clock", "ms")}
+                         for k in ("f64", "f32")},
         "monolithic": mono,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "rswr_run_host (C ABI, pinned host buffers, copies inside the timed region)"},

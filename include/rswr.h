@@ -350,14 +350,38 @@ rswr_status rswr_batch_adjoint(rswr_batch_t batch, const void* fA, const void* f
  *   fA, fB   device, T+1 Dirichlet samples each, or NULL (zero)
  *   q0, q1   device initial state pair or NULL (zero data / at rest)
  *   out0, out1  device final state pair (required)
+ *   stream   a cudaStream_t of the CURRENT device, or NULL (legacy stream);
+ *            a stream of another device is rejected with RSWR_EINVAL
  * The first call on each device looks up the scratch area's device address
- * (with that device current); make that first call before any stream
- * capture.  All calls share the scratch area and each clears what must start
+ * (with that device current) and remembers it; make that first call before
+ * any stream capture.  After cudaDeviceReset on a device the remembered
+ * address is stale: load the library again before calling this on that
+ * device.  All calls share the scratch area and each clears what must start
  * at zero; calls whose work overlaps on the GPU race and give wrong results.
+ * The call returns once its work on `stream` has finished: it reads the
+ * device error record back, and a bounded device wait that ran out of time
+ * is reported as RSWR_ETIMEOUT.
  */
 rswr_status rswr_run_noalloc(double xa, double xb, double a, int64_t nx, double dt, int32_t n_sub, int32_t overlap,
                              int32_t dtype, const void* fA, const void* fB, int64_t T, const void* q0,
                              const void* q1, void* out0, void* out1, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Measurement utility                                                       */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Arithmetic-pipe throughput probe (not a step of the paper's method): the
+ * denominator of the span kernels' roofline.  Launches `blocks` x `threads`
+ * threads (threads a multiple of 32, at most 1024) on `stream`; each thread
+ * runs 8 independent chains of `iters` fused multiply-adds of `dtype`
+ * (RSWR_F64: the FP64 pipe, RSWR_F32: the FP32 pipe) and writes one value to
+ * sink[thread] (device, blocks * threads elements of dtype, caller-owned).
+ * The call is asynchronous and changes no device setting; the caller times it
+ * with events on `stream`: rate = 8 * iters * blocks * threads / seconds.
+ * Errors: EINVAL (bad sizes, NULL sink, dtype), ECUDA (launch failed).
+ */
+rswr_status rswr_fma_probe(int32_t dtype, int64_t iters, int32_t blocks, int32_t threads, void* sink, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Kernel variants                                                           */

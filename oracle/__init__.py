@@ -44,7 +44,7 @@ def build(force: bool = False) -> str:
         return _LIB
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     tmp = _LIB + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
            "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True, cwd=_HERE)
     os.replace(tmp, _LIB)
@@ -71,6 +71,8 @@ _vp = ctypes.c_void_p
 def _declare(L):
     L.oracle_coeffs.argtypes = [_dbl, _dbl, _dbl, _i64, _dbl] + [_vp] * 7
     L.oracle_coeffs.restype = None
+    L.oracle_set_threads.argtypes = [ctypes.c_int]
+    L.oracle_set_threads.restype = None
     for suf, R in (("f64", _dbl), ("f32", _flt)):
         f = getattr(L, f"oracle_leapfrog_{suf}")
         f.argtypes = [ctypes.c_int, _i64, _i64, R, R, _vp, _vp, _vp, _vp, _vp, _vp,
@@ -107,6 +109,12 @@ class Coeffs:
     kf: np.float32
     inv2dxf: np.float32
     dx: float
+
+
+def set_threads(n: int) -> None:
+    """Threads of the monolithic leapfrog's interior loop (default 1).  The
+    result is the same bit for bit for any count (pinned by the tests)."""
+    lib().oracle_set_threads(int(n))
 
 
 def coeffs(xa: float, xb: float, a: float, nx: int, dt: float) -> Coeffs:

@@ -119,6 +119,7 @@ int NAME(oracle_leapfrog)(int form, int64_t nx, int64_t T, REAL c2, REAL k,
     NAME(init_state)(form, nx, fA, fB, q0, q1, u, w);
     NAME(record)(0, T, u, nrec, rec_j, rec, nflux, flux_j, inv2dx, flux);
     for (int64_t n = 0; n < T; ++n) {
+#pragma omp parallel for schedule(static) num_threads(oracle_nthreads) if (oracle_nthreads > 1)
         for (int64_t j = 1; j < nx - 1; ++j)
             NAME(point_update)(form, c2, k, u[j - 1], u[j], u[j + 1], w[j], &un[j], &wn[j]);
         if (src && nsrc > 0) NAME(add_sources)(form, nx, T, n, nsrc, src_j, src, 1, nx - 2, u, un, wn);

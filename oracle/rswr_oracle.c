@@ -50,6 +50,14 @@ void oracle_coeffs(double xa, double xb, double a, int64_t nx, double dt,
     *inv2dxf = (float)(*inv2dx);
 }
 
+/* Threads of the monolithic leapfrog's interior loop (1 = serial, the
+ * default).  The updates of one level read only the previous levels, so the
+ * result is the same bit for bit for any count; threads only shorten the
+ * CPU timing baseline.  Effective when the file is built with -fopenmp. */
+static int oracle_nthreads = 1;
+
+void oracle_set_threads(int n) { oracle_nthreads = n < 1 ? 1 : n; }
+
 #define REAL double
 #define FMA fma
 #define NAME(x) x##_f64

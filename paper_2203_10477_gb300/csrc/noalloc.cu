@@ -21,6 +21,12 @@
 // call left there: each call clears the parts that must start at zero.  Two
 // calls whose work overlaps on the GPU (for example on two streams without an
 // ordering between them) race on the scratch area and give wrong results.
+//
+// Each call waits for its own work at the end and reads the device error
+// record back (a bounded wait inside a kernel that ran out of time is
+// reported as RSWR_ETIMEOUT).  The remembered device address belongs to the
+// device's current context: after cudaDeviceReset the library has to be
+// loaded again before this entry point is used on that device.
 
 #include <cstring>
 #include <mutex>
@@ -68,6 +74,12 @@ rswr_status scratch_address(void** out)
 }
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// the scratch layout gives the problem record and the error record one
+// 256-byte slot each
+static_assert(sizeof(ProblemDev<double>) <= 256 && sizeof(ProblemDev<float>) <= 256,
+              "problem record larger than its scratch slot");
+static_assert(sizeof(DevError) <= 256, "error record larger than its scratch slot");
 
 // Writes the one-problem table and the tile table into the scratch area and
 // clears the device error record.
@@ -211,7 +223,15 @@ rswr_status run_noalloc(const rswr_problem& q, int form, const void* fA, const v
     const int fin = nspans & 1;
     NA_CUDA(cudaMemcpyAsync(out0, st0[fin] + pad, sizeof(Real) * q.nx, cudaMemcpyDeviceToDevice, s));
     NA_CUDA(cudaMemcpyAsync(out1, st1[fin] + pad, sizeof(Real) * q.nx, cudaMemcpyDeviceToDevice, s));
+    // the device error record of this call: wait for the run, then read it
+    DevError h{};
+    NA_CUDA(cudaMemcpyAsync(&h, err, sizeof(h), cudaMemcpyDeviceToHost, s));
+    NA_CUDA(cudaStreamSynchronize(s));
 #undef NA_CUDA
+    if (h.code == kDevTimeoutLoad || h.code == kDevTimeoutFlag)
+        return nfail(RSWR_ETIMEOUT, "device wait expired (code " + std::to_string(h.code) + ", tile " +
+                                        std::to_string(h.tile) + ", span " + std::to_string(h.span) + ")");
+    if (h.code != 0) return nfail(RSWR_ECUDA, "device error code " + std::to_string(h.code));
     return RSWR_OK;
 }
 
@@ -229,6 +249,14 @@ extern "C" rswr_status rswr_run_noalloc(double xa, double xb, double a, int64_t 
     if (dtype != RSWR_F32 && dtype != RSWR_F64) return nfail(RSWR_EINVAL, "dtype must be RSWR_F32 or RSWR_F64");
     const rswr_problem q{nx, xa, xb, a, dt, n_sub, overlap};
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the scratch address and the launch size come from the current device,
+    // so the stream must belong to it
+    if (s) {
+        int cur = -1, sdev = -1;
+        if (cudaGetDevice(&cur) != cudaSuccess || cudaStreamGetDevice(s, &sdev) != cudaSuccess)
+            return nfail(RSWR_ECUDA, "cannot query the device of the stream");
+        if (cur != sdev) return nfail(RSWR_EINVAL, "the stream belongs to another device than the current one");
+    }
     if (dtype == RSWR_F64) return run_noalloc<double>(q, kCanonical, fA, fB, T, q0, q1, out0, out1, s);
     return run_noalloc<float>(q, kIncrement, fA, fB, T, q0, q1, out0, out1, s);
 }

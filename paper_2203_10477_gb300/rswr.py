@@ -100,6 +100,7 @@ SIGNATURES = {
     "rswr_batch_check": (_st, [_vp, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "rswr_batch_run": (_st, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "rswr_batch_adjoint": (_st, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]),
+    "rswr_fma_probe": (_st, [_i32, _i64, _i32, _i32, _vp, _vp]),
     "rswr_variant_count": (_i32, []),
     "rswr_variant_get": (_st, [_i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                                ctypes.POINTER(_i32)]),
@@ -202,6 +203,40 @@ def variants() -> list[dict]:
         out.append({"variant": v, "dtype": d.value, "form": f.value, "P": p.value, "NT": n.value,
                     "KH": kh.value, "window": w.value, "max_span": ms.value, "threads": th.value})
     return out
+
+
+def fma_rate(dtype, device=None, target_ms=60.0, reps=3) -> dict:
+    """Fused multiply-adds per second of the FP64 (dtype F64) or FP32 (F32)
+    pipe on `device`, measured with rswr_fma_probe: 8 blocks of 256 threads
+    per SM, the iteration count sized to about `target_ms`, best of `reps`
+    launches timed with CUDA events on the current stream."""
+    torch = _torch()
+    dev = torch.device("cuda" if device is None else device)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads = 8 * sms, 256
+    td = torch.float64 if dtype == F64 else torch.float32
+    with torch.cuda.device(dev):
+        sink = torch.empty(blocks * threads, dtype=td, device=dev)
+        stream = torch.cuda.current_stream(dev)
+
+        def launch(iters):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            check(lib().rswr_fma_probe(dtype, iters, blocks, threads, _ptr(sink), _stream(stream)))
+            e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1)
+
+        iters = 256
+        ms = launch(iters)
+        while ms < 5.0:
+            iters *= 4
+            ms = launch(iters)
+        iters = max(1, int(iters * target_ms / ms))
+        best = min(launch(iters) for _ in range(reps))
+    fmas = 8.0 * iters * blocks * threads
+    return {"fma_per_s": fmas / (best / 1e3), "ms": best, "iters": iters, "blocks": blocks, "threads": threads,
+            "sms": sms, "finite": bool(torch.isfinite(sink).all())}
 
 
 class Plan:
@@ -481,30 +516,37 @@ def _make_function():
     torch = _torch()
 
     class RSWRFunction(torch.autograd.Function):
-        """recv = RSWRFunction.apply(fA, a, plan, T, j_r): the receiver trace of an
-        RSWR run as a differentiable function of the left boundary waveform fA and
-        of the wave speed a (a one-element tensor equal to the plan's speed).
-        Backward calls rswr_adjoint (the library's adjoint kernels)."""
+        """recv = RSWRFunction.apply(fA, a, plan, T, j_r[, fB]): the receiver trace
+        of an RSWR run as a differentiable function of the left boundary waveform
+        fA and of the wave speed a (a one-element tensor equal to the plan's
+        speed).  The right boundary waveform fB (T+1 samples, default 0) enters
+        the forward run and the gradient w.r.t. a, but is data: a fB that
+        requires a gradient is refused.  Backward calls rswr_adjoint (the
+        library's adjoint kernels)."""
 
         @staticmethod
-        def forward(ctx, fA, a, plan: Plan, T: int, j_r: int):
+        def forward(ctx, fA, a, plan: Plan, T: int, j_r: int, fB=None):
             if a is not None and abs(float(a) - plan.a) > 1e-15 * max(1.0, abs(plan.a)):
                 raise ValueError("a must equal the plan's wave speed")
+            if fB is not None and fB.requires_grad:
+                raise ValueError("gradients w.r.t. the right boundary waveform fB are not provided")
             fA_d = fA.detach()
-            res = plan.run(fA_d, None, T, j_r=j_r)
-            ctx.save_for_backward(fA_d)
+            fB_d = None if fB is None else fB.detach()
+            res = plan.run(fA_d, fB_d, T, j_r=j_r)
+            ctx.save_for_backward(fA_d, fB_d)
             ctx.plan, ctx.T, ctx.j_r, ctx.want_a = plan, T, j_r, a is not None and a.requires_grad
             ctx.a_shape = None if a is None else a.shape
+            ctx.n_inputs = 6 if fB is not None else 5
             return res["recv"]
 
         @staticmethod
         def backward(ctx, grad_out):
-            (fA,) = ctx.saved_tensors
-            g = ctx.plan.adjoint(fA, None, ctx.T, ctx.j_r, grad_out.contiguous(), want_a=ctx.want_a)
+            fA, fB = ctx.saved_tensors
+            g = ctx.plan.adjoint(fA, fB, ctx.T, ctx.j_r, grad_out.contiguous(), want_a=ctx.want_a)
             ga = None
             if ctx.want_a:
                 ga = g["grad_a"].reshape(ctx.a_shape).to(grad_out.dtype)
-            return g["grad_fA"], ga, None, None, None
+            return (g["grad_fA"], ga, None, None, None, None)[: ctx.n_inputs]
 
     return RSWRFunction
 

@@ -635,3 +635,32 @@ def test_rswr_mask_with_sources_equals_monolithic_bitwise(oracle_mod, prec, form
     assert np.abs(mono["u"]).max() > 0.1
     assert np.array_equal(rs["u"], mono["u"])
     assert np.array_equal(rs["w"], mono["w"])
+
+
+# ----------------------------------------------------------------------------
+# the threaded interior loop (the CPU timing baseline on all host cores)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("form", [CAN, INC])
+def test_threaded_leapfrog_equals_serial_bitwise(oracle_mod, form, prec):
+    """The interior updates of one level are independent, so the threaded
+    loop gives the serial result bit for bit (state, probes, sources)."""
+    nx, T = 200_003, 40
+    dt = 0.9 / (nx - 1)
+    q0 = inputs.smooth_random_state(nx, seed=11)
+    fA = inputs.ramped_sine(T, dt, freq=30.0)
+    fB = inputs.ramped_sine(T, dt, freq=11.0)
+    smp = np.stack([inputs.gaussian_pulse(T, dt, sigma_steps=4), -inputs.gaussian_pulse(T, dt, sigma_steps=6)])
+    kw = dict(form=form, prec=prec, q0=q0, rec_j=[5, 100_000], flux_j=[77, 150_000], src_j=[1000, 123_456],
+              src=smp)
+    oracle_mod.set_threads(1)
+    ser = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, fB, **kw)
+    oracle_mod.set_threads(4)
+    try:
+        par = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, fB, **kw)
+    finally:
+        oracle_mod.set_threads(1)
+    for key in ("u", "w", "rec", "flux"):
+        assert np.array_equal(ser[key], par[key]), key
+    assert np.abs(ser["u"]).max() > 0.1
