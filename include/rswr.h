@@ -109,6 +109,25 @@ typedef struct rswr_plan_s* rswr_plan_t;
 rswr_status rswr_plan_create(rswr_plan_t* plan, double xa, double xb, double a, int64_t nx, double dt,
                              int32_t n_sub, int32_t overlap, int32_t dtype, int32_t form, uint32_t flags);
 
+/* Creates a plan for the part [lo, hi) of the grid of (xa, xb, nx): the
+ * building block of one problem split over several GPUs (paper Sec. 3: the
+ * subdomains in a row; a GPU keeps a block of them plus halo points).  The
+ * part has hi - lo points with the spacing and the stencil coefficients of
+ * the whole grid (c = a dt / dx, dx = (xb - xa)/(nx - 1)), decomposed into its
+ * own n_sub subdomains sharing `overlap` points.  Its two end nodes are
+ * Dirichlet nodes of rswr_run: fA drives point lo, fB point hi - 1.  At
+ * lo = 0 / hi = nx they are the problem's own boundary nodes; at a cut they
+ * hold a guess, whose influence travels one point per step, so a run of s
+ * steps from the true state is exact on [lo + s, hi - 1 - s] (the Waveform
+ * Time Span Theorem, Sec. 2.4, applied to the part as a window).  Results of
+ * a part equal the whole grid's on those points bit for bit.
+ * rswr_run_paper is not available on a part (RSWR_ENOTSUP).
+ * Errors: as rswr_plan_create, and EINVAL unless 0 <= lo, hi <= nx and
+ * hi - lo >= 3; ECFL is checked on the whole grid. */
+rswr_status rswr_plan_create_part(rswr_plan_t* plan, double xa, double xb, double a, int64_t nx, double dt,
+                                  int64_t lo, int64_t hi, int32_t n_sub, int32_t overlap, int32_t dtype, int32_t form,
+                                  uint32_t flags);
+
 /* Frees the plan and its workspace (synchronises the device first). NULL is a no-op. */
 void rswr_plan_destroy(rswr_plan_t plan);
 

@@ -90,6 +90,7 @@ struct Engine {
     int S = 1, H = 4, W = 0, core = 0, P = 0, NT = 0;
     int inject_tile = -1, inject_span = -1;
     bool is_plan = true;
+    bool part = false;  // a part [lo, hi) of a larger grid (rswr_plan_create_part)
 
     std::vector<ProbHost> probs;
     int64_t ntiles = 0, state_len = 0, packed_len = 0;
@@ -1640,6 +1641,39 @@ rswr_status rswr_plan_create(rswr_plan_t* plan, double xa, double xb, double a, 
     return RSWR_OK;
 }
 
+rswr_status rswr_plan_create_part(rswr_plan_t* plan, double xa, double xb, double a, int64_t nx, double dt,
+                                  int64_t lo, int64_t hi, int32_t n_sub, int32_t overlap, int32_t dtype, int32_t form,
+                                  uint32_t flags)
+{
+    if (!plan) return fail(RSWR_EINVAL, "plan is NULL");
+    *plan = nullptr;
+    (void)flags;
+    if (lo < 0 || hi > nx || hi - lo < 3) return fail(RSWR_EINVAL, "need 0 <= lo, hi <= nx and hi - lo >= 3");
+    // the whole grid fixes the coefficients (and the Courant-number check)
+    const rswr_problem g{nx, xa, xb, a, dt, 1, 2};
+    rswr_status st = validate(g);
+    if (st != RSWR_OK) return st;
+    ProbHost whole{};
+    whole.nx = nx; whole.xa = xa; whole.xb = xb; whole.a = a; whole.dt = dt;
+    coefficients(whole);
+    // the part: hi - lo points of the same spacing, its own decomposition
+    const double dx = (xb - xa) / (double)(nx - 1);
+    const rswr_problem q{hi - lo, xa + (double)lo * dx, xa + (double)(hi - 1) * dx, a, dt, n_sub, overlap};
+    Engine* e = nullptr;
+    st = make_engine(&e, 1, &q, dtype, form, true);
+    if (st != RSWR_OK) return st;
+    ProbHost& ph = e->probs[0];
+    ph.c = whole.c; ph.c2 = whole.c2; ph.k = whole.k; ph.inv2dx = whole.inv2dx;
+    ph.c2f = whole.c2f; ph.kf = whole.kf; ph.inv2dxf = whole.inv2dxf;
+    e->part = true;
+    *plan = new (std::nothrow) rswr_plan_s{e};
+    if (!*plan) {
+        free_engine(e);
+        return fail(RSWR_ENOMEM, "host allocation");
+    }
+    return RSWR_OK;
+}
+
 void rswr_plan_destroy(rswr_plan_t plan)
 {
     if (!plan) return;
@@ -1977,6 +2011,7 @@ rswr_status rswr_run_paper(rswr_plan_t plan, const void* fA, const void* fB, int
     const ProbHost& ph = e->probs[0];
     if (ph.ov + 64 > 2048) return fail(RSWR_EINVAL, "paper-literal path supports overlaps up to 1984 points");
     if (!e->usrc.empty()) return fail(RSWR_ENOTSUP, "the paper-literal path runs without user point sources");
+    if (e->part) return fail(RSWR_ENOTSUP, "the paper-literal path runs on whole grids only");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (e->dtype == kF64)
         return run_paper<double>(e, static_cast<const double*>(fA), static_cast<const double*>(fB), T,

@@ -67,6 +67,8 @@ SIGNATURES = {
     "rswr_version": (_i32, []),
     "rswr_plan_create": (_st, [ctypes.POINTER(_vp), _dbl, _dbl, _dbl, _i64, _dbl, _i32, _i32, _i32, _i32,
                                ctypes.c_uint32]),
+    "rswr_plan_create_part": (_st, [ctypes.POINTER(_vp), _dbl, _dbl, _dbl, _i64, _dbl, _i64, _i64, _i32, _i32, _i32,
+                                    _i32, ctypes.c_uint32]),
     "rswr_plan_destroy": (None, [_vp]),
     "rswr_plan_get_info": (_st, [_vp, ctypes.POINTER(PlanInfo)]),
     "rswr_plan_set_span": (_st, [_vp, _i32]),
@@ -257,6 +259,24 @@ class Plan:
     @classmethod
     def from_problem(cls, p, dtype=F64, form=FORM_DEFAULT, device=None):
         return cls(p.xa, p.xb, p.a, p.nx, p.dt, p.n_sub, p.overlap, dtype, form, device)
+
+    @classmethod
+    def part(cls, xa, xb, a, nx, dt, lo, hi, n_sub, overlap, dtype=F64, form=FORM_DEFAULT, device=None):
+        """A plan for the points [lo, hi) of the grid (xa, xb, nx) with the whole
+        grid's coefficients (rswr_plan_create_part)."""
+        torch = _torch()
+        self = cls.__new__(cls)
+        self.device = torch.device("cuda" if device is None else device)
+        self.dtype = dtype
+        h = _vp()
+        with torch.cuda.device(self.device):
+            check(lib().rswr_plan_create_part(ctypes.byref(h), xa, xb, a, nx, dt, lo, hi, n_sub, overlap, dtype,
+                                              form, 0))
+        self.h = h
+        self.nx = hi - lo
+        self.n_sub = n_sub
+        self.a = a
+        return self
 
     def close(self):
         if getattr(self, "h", None):
