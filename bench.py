@@ -93,7 +93,9 @@ def measured_traffic(dtype: str, variant: int, span: int):
 # dL/dfA alone: the adjoint variables through the same span kernel;
 # dL/dfA and dL/da: checkpoint sweep (3 / 4) + adjoint kernel (recompute 3 / 4, Laplacian
 # 1 / 0 (the increment form's second difference is the Laplacian), pairing 1, adjoint step 3 / 4).
-ADJ_OPS = {"f64": {"g": 3, "full": 3 + 3 + 1 + 1 + 3}, "f32": {"g": 4, "full": 4 + 4 + 0 + 1 + 4}}
+# after a kept forward run (rswr_run_keep) the gradient skips the checkpoint sweep.
+ADJ_OPS = {"f64": {"g": 3, "full": 3 + 3 + 1 + 1 + 3, "after_keep": 3 + 1 + 1 + 3},
+           "f32": {"g": 4, "full": 4 + 4 + 0 + 1 + 4, "after_keep": 4 + 0 + 1 + 4}}
 
 
 # FMA rates of the two pipes measured on this device by rswr_fma_probe (set in main)
@@ -270,9 +272,11 @@ def cpu_baseline(p, budget_s: float = 10.0) -> dict:
     oracle.build()
     res = {}
     for cores in (host_cores(), 1):
-        oracle_sample(p, 2, cores)  # start the threads, touch the pages
-        t8 = oracle_sample(p, 8, cores)
-        steps = int(max(8, min(p.T, budget_s / max(t8 / 8, 1e-9))))
+        oracle_sample(p, 2, cores)  # start the threads
+        # each call allocates and first-touches its arrays: calibrate on enough
+        # steps that this start-up cost is a small part
+        t64 = oracle_sample(p, 64, cores)
+        steps = int(max(64, min(p.T, budget_s / max(t64 / 64, 1e-9))))
         secs = oracle_sample(p, steps, cores)
         res[cores] = ((p.nx - 2) * steps / secs / 1e9, steps, secs)
     n = host_cores()
@@ -293,9 +297,9 @@ def run_reference(args, rank: int, world: int) -> None:
 
     oracle.build()
     cores = host_cores()
-    oracle_sample(p, 2, cores)  # start the threads, touch the pages
-    t8 = oracle_sample(p, 8, cores)
-    steps_per = int(max(8, min(p.T, 4.0 / max(t8 / 8, 1e-9))))  # about 4 s of CPU work per step
+    oracle_sample(p, 2, cores)  # start the threads
+    t64 = oracle_sample(p, 64, cores)
+    steps_per = int(max(64, min(p.T, 4.0 / max(t64 / 64, 1e-9))))  # about 4 s of CPU work per step
     for _ in range(args.warmup):
         oracle_sample(p, steps_per, cores)
     times = [oracle_sample(p, steps_per, cores) for _ in range(args.steps)]
@@ -666,10 +670,16 @@ def bench_adjoint(torch, dev):
             last["r"] = plan.adjoint(fA, None, p.T, 4000, wt, want_a=True)
 
         gonly = lambda: plan.adjoint(fA, None, p.T, 4000, wt, want_a=False)
+        fwd_keep = lambda: plan.run_keep(fA, None, p.T, j_r=4000)
         full()
         gonly()
         ms_full = _time(torch, full, 2)
         ms_g = _time(torch, gonly, 2)
+        # the training pattern: a forward run that keeps its span states, then the gradient
+        ms_keep, ms_after = [], []
+        for _ in range(2):
+            ms_keep += _time(torch, fwd_keep, 1)
+            ms_after += _time(torch, full, 1)
         plan.check()
         lups = (p.nx - 2) * p.T
         v_full = lups / (min(ms_full) / 1e3) / 1e9
@@ -678,6 +688,13 @@ def bench_adjoint(torch, dev):
                                        "roofline": alu_roofline(name, v_full, ADJ_OPS[name]["full"])},
                      "grad_fA_only": {"value": v_g, "ms": min(ms_g),
                                       "roofline": alu_roofline(name, v_g, ADJ_OPS[name]["g"])}}
+        v_after = lups / (min(ms_after) / 1e3) / 1e9
+        v_pair = lups / ((min(ms_keep) + min(ms_after)) / 1e3) / 1e9
+        res[name]["grad_fA_and_a_after_kept_forward"] = {
+            "value": v_after, "ms": min(ms_after), "roofline": alu_roofline(name, v_after, ADJ_OPS[name]["after_keep"]),
+            "kept_forward_ms": min(ms_keep), "forward_and_gradient_value": v_pair,
+            "note": "rswr_run_keep (forward, span states kept) then rswr_adjoint with dL/da, which skips its "
+                    "checkpoint sweep; value counts the gradient call alone"}
         # checker leg: the gradients of the last timed run against the FP64 oracle's adjoint
         g = last["r"]["grad_fA"].double().cpu().numpy()
         ga = float(last["r"]["grad_a"][0])

@@ -271,6 +271,26 @@ rswr_status rswr_mono(rswr_plan_t plan, const void* fA, const void* fB, int64_t 
                       void* out0, void* out1, void* traces, int64_t j_r, void* recv, void* stream);
 
 /*
+ * A forward run kept for the gradient that follows it (not in the paper; the
+ * training pattern of the gradient workload): zero initial data, Dirichlet
+ * samples fA, fB (T+1 each, NULL = 0), final state pair into out0/out1 and,
+ * when recv is not NULL, the receiver trace u^n_{j_r}, n = 0..T, into recv --
+ * the same values as rswr_run, bit for bit.  It runs the sweep that
+ * rswr_adjoint with dL/da needs first (spans of the adjoint's length, every
+ * span-boundary state stored in the plan's workspace) and keeps those states:
+ * a following rswr_adjoint with grad_a on the same plan, with the same fA and
+ * fB pointers and the same T, skips its own forward sweep.  The caller must
+ * not change the contents of fA or fB in between.  A call with other
+ * pointers, another T, a changed span, variant or checkpoint spacing, or a
+ * paper-literal run in between discards the kept states; rswr_adjoint then
+ * sweeps again (same results).  When the states do not fit in device memory
+ * this is a plain rswr_run and nothing is kept.
+ * Errors: as rswr_run; ENOTSUP while user point sources are set.
+ */
+rswr_status rswr_run_keep(rswr_plan_t plan, const void* fA, const void* fB, int64_t T, int64_t j_r, void* recv,
+                          void* out0, void* out1, void* stream);
+
+/*
  * Discrete adjoint (not in the paper; the gradient workload of this library).
  * For the receiver trace y^n = u^n_{j_r} of a zero-data run with Dirichlet
  * samples fA, fB, and a cotangent wbar = dL/dy (T+1 values), computes

@@ -119,6 +119,25 @@ struct Engine {
     // adjoint workspace (rswr_adjoint with dL/da): states, tables, partial sums
     void* adj_mem = nullptr;
     size_t adj_mem_cap = 0;
+    // Span states of a forward run kept in adj_mem for the next rswr_adjoint
+    // (rswr_run_keep): valid while `kept` holds and the key matches.
+    struct KeptKey {
+        const void* fA;
+        const void* fB;
+        int64_t T;
+        int SA, vf, va, core_f, core_a;
+        int64_t C;
+        bool ws;
+        size_t arr, need;
+        bool operator==(const KeptKey& o) const
+        {
+            return fA == o.fA && fB == o.fB && T == o.T && SA == o.SA && vf == o.vf && va == o.va &&
+                   core_f == o.core_f && core_a == o.core_a && C == o.C && ws == o.ws && arr == o.arr &&
+                   need == o.need;
+        }
+    };
+    bool kept = false;
+    KeptKey kept_key{};
     // CUDA graph of the last run's device work, replayed while the arguments repeat
     bool use_graph = true;
     cudaStream_t cap_stream = nullptr;
@@ -964,9 +983,18 @@ namespace {
 //   per segment of C spans, last first: the span kernel recomputes the state at
 //   the start of every span of the segment, then the adjoint kernel runs the
 //   segment's spans last first (reversed-time adjoint levels ascending).
+// Forward-only use of the sweep below (rswr_run_keep): keep every span state,
+// record the receiver trace, write the final state pair.
+struct KeepReq {
+    int64_t j_rec;  // receiver grid index, or -1
+    void* recv;     // T+1 samples, or NULL
+    void* out0;
+    void* out1;
+};
+
 template <typename Real>
 rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* fA, const void* fB, const void* wbar,
-                         void* grad, double* grad_a, cudaStream_t s)
+                         void* grad, double* grad_a, cudaStream_t s, const KeepReq* keep = nullptr)
 {
     const int np = (int)e->probs.size();
     const size_t es = sizeof(Real);
@@ -1042,6 +1070,7 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
         make_layout(ai.W - 2 * H);
         C = spacing();
     }
+    if (keep && C != 1) return fail(RSWR_ENOMEM, "the span states of this run do not fit in device memory");
     const int64_t nck = std::max<int64_t>(1, (nspans + C - 1) / C);
     const int64_t nstates = nck + C + 4;  // checkpoints | segment | forward work pair | adjoint pair
 
@@ -1050,11 +1079,16 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     const size_t b_partial = up(sizeof(double) * std::max<int64_t>(nspans, 1) * nta);
     const size_t b_tiles = up(sizeof(TileDev) * (ntf + nta));
     const size_t b_prob = up(sizeof(ProblemDev<Real>) * 2 * np);
-    const size_t b_probes = up(sizeof(ProbeDev<Real>) * np);
+    const size_t b_probes = up(sizeof(ProbeDev<Real>) * (np + 1));  // adjoint probes | forward receiver
     const size_t b_red = up(sizeof(int64_t) * 2 * np + sizeof(double) * np);
     const size_t b_done = up(sizeof(int) * std::max<int64_t>(ntf, nta));
     const size_t b_rtmp = up(sizeof(double) * (size_t)adj_reduce_blocks(std::max<int64_t>(nspans, 1), np) * np);
     const size_t need = b_states + b_partial + b_tiles + b_prob + b_probes + b_red + b_done + b_rtmp;
+    // the span states of an earlier sweep with the same inputs and layout are
+    // still in the workspace: the forward sweep can be skipped
+    const Engine::KeptKey key{fA, fB, T, SA, vf, va, core_f, core_a, C, use_ws, arr, need};
+    const bool reuse = !keep && e->kept && e->kept_key == key && need <= e->adj_mem_cap;
+    if (!reuse) e->kept = false;
     if (need > e->adj_mem_cap) {
         RSWR_CUDA(cudaStreamSynchronize(s));
         cudaFree(e->adj_mem);
@@ -1135,12 +1169,26 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
         l.fA = nullptr;
         l.fB = nullptr;
         l.js = interior ? j_r[p] : -1;
-        l.src = static_cast<const Real*>(wbar) + (int64_t)p * (T + 1) + T + 1;
+        l.src = wbar ? static_cast<const Real*>(wbar) + (int64_t)p * (T + 1) + T + 1 : nullptr;
         l.src_stride = -1;
         hscale[p] = 2.0 * ph.c2 / ph.a;
     }
-    // tile-local probe indices were assigned in adjoint-tile order; shift the
-    // forward tiles' empty ranges are already (0, 0)
+    // the forward tiles carry no probes, except the receiver of a kept forward run
+    int fwd_probe = -1;
+    if (keep && keep->recv && np == 1) {
+        fwd_probe = (int)hp.size();
+        ProbeDev<Real> pr{};
+        pr.gidx = base[0] + keep->j_rec;
+        pr.out = static_cast<Real*>(keep->recv);
+        pr.stride = 1;
+        pr.nmax = T;
+        pr.scale = (Real)1;
+        pr.kind = 0;
+        hp.push_back(pr);
+        TileDev& td = ht[t0f[0] + keep->j_rec / core_f];
+        td.probe_begin = fwd_probe;
+        td.probe_end = fwd_probe + 1;
+    }
     RSWR_CUDA(cudaMemcpyAsync(d_tiles_f, ht.data(), sizeof(TileDev) * ht.size(), cudaMemcpyHostToDevice, s));
     RSWR_CUDA(cudaMemcpyAsync(d_pu, hpr.data(), sizeof(ProblemDev<Real>) * hpr.size(), cudaMemcpyHostToDevice, s));
     if (!hp.empty())
@@ -1154,14 +1202,16 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     RSWR_CUDA(cudaMemcpyAsync(d_scale, hscale.data(), sizeof(double) * np, cudaMemcpyHostToDevice, s));
     RSWR_CUDA(cudaMemsetAsync(e->d_err, 0, sizeof(DevError), s));
 
-    // dL/dfA: zero, or wbar itself for a receiver on the left Dirichlet node
-    RSWR_CUDA(cudaMemsetAsync(grad, 0, es * (T + 1) * np, s));
-    for (int p = 0; p < np; ++p)
-        if (j_r[p] == 0)
-            RSWR_CUDA(cudaMemcpyAsync(static_cast<char*>(grad) + es * (T + 1) * p,
-                                      static_cast<const char*>(wbar) + es * (T + 1) * p, es * (T + 1),
-                                      cudaMemcpyDeviceToDevice, s));
-    RSWR_CUDA(cudaMemsetAsync(partial, 0, b_partial, s));
+    if (!keep) {
+        // dL/dfA: zero, or wbar itself for a receiver on the left Dirichlet node
+        RSWR_CUDA(cudaMemsetAsync(grad, 0, es * (T + 1) * np, s));
+        for (int p = 0; p < np; ++p)
+            if (j_r[p] == 0)
+                RSWR_CUDA(cudaMemcpyAsync(static_cast<char*>(grad) + es * (T + 1) * p,
+                                          static_cast<const char*>(wbar) + es * (T + 1) * p, es * (T + 1),
+                                          cudaMemcpyDeviceToDevice, s));
+        RSWR_CUDA(cudaMemsetAsync(partial, 0, b_partial, s));
+    }
 
     int bps_f = 0, bps_a = 0;
     RSWR_CUDA(span_occupancy(vf, &bps_f));
@@ -1172,7 +1222,7 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     SpanParams<Real> fp{};
     fp.problems = d_pu;
     fp.tiles = d_tiles_f;
-    fp.probes = nullptr;
+    fp.probes = fwd_probe >= 0 ? d_probes : nullptr;
     fp.ntiles = ntf;
     fp.T = T;
     fp.H = H;
@@ -1193,10 +1243,11 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
         return RSWR_OK;
     };
 
-    // forward sweep with checkpoints
+    // forward sweep with checkpoints (skipped when an earlier sweep's states are kept)
+    const int64_t last_ck_span = (nck - 1) * C;
+    if (!reuse) {
     RSWR_CUDA(cudaMemsetAsync(state0(CK0), 0, 2 * arr, s));
     RSWR_CUDA(set_boundary_launch(e->dtype, e->form, state0(CK0), state1(CK0), d_pu, np, s));
-    const int64_t last_ck_span = (nck - 1) * C;
     if (C == 1 && last_ck_span > 0) {
         // every span state is kept: the whole sweep is one persistent launch in
         // which span k reads state k and writes state k + 1 (neighbour flags as in
@@ -1221,6 +1272,32 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
             rswr_status st = forward_span(k, state0(si), state1(si), state0(di), state1(di));
             if (st != RSWR_OK) return st;
         }
+    }
+    }
+    // only a kept forward run (rswr_run_keep) leaves states for a later call: an
+    // ordinary adjoint call must not, since its caller may change fA in place
+    if (keep) {
+        e->kept = true;
+        e->kept_key = key;
+    }
+
+    if (keep) {
+        // a kept forward run: the last span into the work pair, the receiver's
+        // last level, the final state pair
+        Real* f0 = state0(CK0);
+        Real* f1 = state1(CK0);
+        if (nspans > 0) {
+            const int64_t k = nspans - 1;  // C == 1: state k is checkpoint k
+            rswr_status st = forward_span(k, state0(CK0 + k), state1(CK0 + k), state0(WK0), state1(WK0));
+            if (st != RSWR_OK) return st;
+            f0 = state0(WK0);
+            f1 = state1(WK0);
+        }
+        if (fwd_probe >= 0) RSWR_CUDA(probe_final_launch(e->dtype, d_probes + fwd_probe, 1, f0, T, s));
+        const int64_t nx = e->probs[0].nx;
+        RSWR_CUDA(cudaMemcpyAsync(keep->out0, f0 + base[0], es * nx, cudaMemcpyDeviceToDevice, s));
+        RSWR_CUDA(cudaMemcpyAsync(keep->out1, f1 + base[0], es * nx, cudaMemcpyDeviceToDevice, s));
+        return RSWR_OK;
     }
 
     // adjoint sweep
@@ -1469,6 +1546,7 @@ rswr_status run_paper(Engine* e, const Real* fA, const Real* fB, int64_t T, cons
     const ProbHost& ph = e->probs[0];
     const int64_t nx = ph.nx, N = ph.n_sub, ov = ph.ov, el = (ov + 1) / 2, er = ov / 2;
     const size_t es = sizeof(Real);
+    e->kept = false;  // the workspace below overwrites kept span states
     int64_t cap = (int64_t)std::ceil((double)(ov - 1) / (2.0 * ph.c)) - 1;
     if (cap < 1) cap = 1;
     int64_t tau = ov;
@@ -1827,6 +1905,32 @@ rswr_status rswr_run_host(rswr_plan_t plan, const void* fA, const void* fB, int6
     if (traces) RSWR_CUDA(cudaMemcpyAsync(traces, dtr, es * ntr, cudaMemcpyDeviceToHost, s));
     if (recv) RSWR_CUDA(cudaMemcpyAsync(recv, drc, es * (T + 1), cudaMemcpyDeviceToHost, s));
     return check_engine(e, s, nullptr, nullptr, nullptr);
+}
+
+rswr_status rswr_run_keep(rswr_plan_t plan, const void* fA, const void* fB, int64_t T, int64_t j_r, void* recv,
+                          void* out0, void* out1, void* stream)
+{
+    if (!plan) return fail(RSWR_EINVAL, "NULL plan");
+    Engine* e = plan->e;
+    if (T < 0 || T > ((int64_t)1 << 40)) return fail(RSWR_EINVAL, "T out of range");
+    if (!out0 || !out1) return fail(RSWR_EINVAL, "out0 and out1 are required");
+    if (recv && (j_r < 0 || j_r >= e->probs[0].nx)) return fail(RSWR_EINVAL, "receiver index outside the grid");
+    if (!e->usrc.empty()) return fail(RSWR_ENOTSUP, "a kept run has no user point sources");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int v = 0; v < adj_variant_count(); ++v) {
+        cudaError_t ce = adj_prepare(v);
+        if (ce != cudaSuccess) return fail(RSWR_ECUDA, std::string("adjoint attributes: ") + cudaGetErrorString(ce));
+    }
+    const KeepReq k{recv ? j_r : -1, recv, out0, out1};
+    const int64_t none = -1;
+    rswr_status st = e->dtype == kF64 ? adjoint_full<double>(e, T, &none, fA, fB, nullptr, nullptr, nullptr, s, &k)
+                                      : adjoint_full<float>(e, T, &none, fA, fB, nullptr, nullptr, nullptr, s, &k);
+    if (st == RSWR_ENOMEM) {
+        // the span states do not fit: a plain run, nothing kept
+        e->kept = false;
+        return plan_run(e, fA, fB, T, nullptr, nullptr, out0, out1, nullptr, recv ? j_r : -1, recv, stream, false);
+    }
+    return st;
 }
 
 rswr_status rswr_adjoint(rswr_plan_t plan, const void* fA, const void* fB, int64_t T, int64_t j_r, const void* wbar,

@@ -91,6 +91,7 @@ SIGNATURES = {
     "rswr_mono": (_st, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "rswr_run_paper": (_st, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "rswr_adjoint": (_st, [_vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp]),
+    "rswr_run_keep": (_st, [_vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp]),
     "rswr_batch_create": (_st, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(Problem), _i32, _i32, ctypes.c_uint32]),
     "rswr_batch_destroy": (None, [_vp]),
     "rswr_batch_offsets": (_st, [_vp, _vp]),
@@ -362,6 +363,22 @@ class Plan:
         """RSWR run (the hot path).  Returns dict(u, w, traces, recv) of device tensors."""
         return self._run(lib().rswr_run, fA, fB, T, **kw)
 
+    def run_keep(self, fA, fB, T, j_r=None, out=None, stream=None):
+        """A forward run that keeps its span states for the next adjoint with
+        dL/da (rswr_run_keep).  Returns dict(u, w, recv) like run()."""
+        torch = _torch()
+        dev = self.device
+        fA_ = _as_dev(fA, self.dtype, dev)
+        fB_ = _as_dev(fB, self.dtype, dev)
+        td = _tdtype(self.dtype)
+        if out is None:
+            out = (torch.empty(self.nx, dtype=td, device=dev), torch.empty(self.nx, dtype=td, device=dev))
+        rec = torch.empty(T + 1, dtype=td, device=dev) if j_r is not None else None
+        with torch.cuda.device(dev):
+            check(lib().rswr_run_keep(self.h, _ptr(fA_), _ptr(fB_), T, -1 if j_r is None else int(j_r), _ptr(rec),
+                                      _ptr(out[0]), _ptr(out[1]), _stream(stream)))
+        return {"u": out[0], "w": out[1], "recv": rec, "_keep": (fA_, fB_)}
+
     def run_paper(self, fA, fB, T, q0=None, q1=None, out=None, stream=None):
         """The paper-literal RSWR (data-chosen spans).  Returns dict(u, w, spans)."""
         torch = _torch()
@@ -550,11 +567,15 @@ def _make_function():
                 raise ValueError("a must equal the plan's wave speed")
             if fB is not None and fB.requires_grad:
                 raise ValueError("gradients w.r.t. the right boundary waveform fB are not provided")
-            fA_d = fA.detach()
-            fB_d = None if fB is None else fB.detach()
-            res = plan.run(fA_d, fB_d, T, j_r=j_r)
+            # the plan's dtype on its device, so that backward passes the very
+            # arrays the forward run read
+            fA_d = _as_dev(fA.detach(), plan.dtype, plan.device)
+            fB_d = None if fB is None else _as_dev(fB.detach(), plan.dtype, plan.device)
+            want_a = a is not None and a.requires_grad
+            # with dL/da wanted, the forward run keeps its span states for backward
+            res = (plan.run_keep if want_a else plan.run)(fA_d, fB_d, T, j_r=j_r)
             ctx.save_for_backward(fA_d, fB_d)
-            ctx.plan, ctx.T, ctx.j_r, ctx.want_a = plan, T, j_r, a is not None and a.requires_grad
+            ctx.plan, ctx.T, ctx.j_r, ctx.want_a = plan, T, j_r, want_a
             ctx.a_shape = None if a is None else a.shape
             ctx.n_inputs = 6 if fB is not None else 5
             return res["recv"]

@@ -852,3 +852,62 @@ def test_c1_equals_the_stored_oracle_values(R):
            "trace_right": [(n, tr[0, 1, n]) for n in make_golden.LEVELS]}
     for key, rows in got.items():
         assert [(i, float(v)) for i, v in rows] == stored[key], key
+
+
+# ----------------------------------------------------------------------------
+# a forward run kept for the gradient (rswr_run_keep)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", [F64, F32])
+@pytest.mark.parametrize("nx,N,ov,T,jr", [
+    (301, 3, 16, 420, 120),      # 53 spans of 8 (FP64) / 27 of 16 (FP32)
+    (2001, 4, 64, 2003, 777),    # ragged last span
+    (301, 3, 16, 5, 2),          # one short span
+    (301, 3, 16, 0, 2),          # no step
+])
+def test_run_keep_equals_run_and_the_adjoint_reuses_it(R, oracle_mod, dtype, nx, N, ov, T, jr):
+    a = 1.3
+    dt = 0.9 / (nx - 1) / a
+    td = torch.float64 if dtype == F64 else torch.float32
+    g = torch.tensor(inputs.lowpass_noise(T, seed=21), dtype=td, device="cuda")
+    fB = torch.tensor(inputs.ramped_sine(T, dt, freq=3.0) * 0.3, dtype=td, device="cuda")
+    w = torch.tensor(inputs.rng(5).standard_normal(T + 1), dtype=td, device="cuda")
+    plan = R.Plan(0.0, 1.0, a, nx, dt, N, ov, dtype=dtype)
+    ref = plan.run(g, fB, T, j_r=jr)
+    ref = {k: ref[k].clone() for k in ("u", "w", "recv")}
+    fresh = plan.adjoint(g, fB, T, jr, w, want_a=True)
+    fresh = {k: fresh[k].clone() for k in ("grad_fA", "grad_a")}
+    kept = plan.run_keep(g, fB, T, j_r=jr)
+    for k in ("u", "w", "recv"):
+        assert torch.equal(kept[k], ref[k]), f"rswr_run_keep {k} differs from rswr_run"
+    for _ in range(2):  # the kept states serve more than one cotangent
+        got = plan.adjoint(g, fB, T, jr, w, want_a=True)
+        plan.check()
+        assert torch.equal(got["grad_fA"], fresh["grad_fA"])
+        assert torch.equal(got["grad_a"], fresh["grad_a"])
+    if dtype == F64 and T > 0:
+        o = oracle_mod.adjoint(nx, T, a, dt, host(g), host(fB), jr, host(w))
+        assert_bitwise(host(got["grad_fA"]), o["dg"], "grad_fA after a kept run")
+        assert abs(float(got["grad_a"][0]) - o["da"]) <= 1e-12 * o["abs_da"]
+
+
+def test_adjoint_after_run_keep_with_other_inputs_sweeps_again(R, oracle_mod):
+    """Other boundary samples (another pointer) than the kept run's: the adjoint
+    does its own forward sweep and matches the oracle for its own inputs."""
+    nx, N, ov, T, jr, a = 301, 3, 16, 420, 120, 1.3
+    dt = 0.9 / (nx - 1) / a
+    g1 = torch.tensor(inputs.lowpass_noise(T, seed=1), dtype=torch.float64, device="cuda")
+    g2 = torch.tensor(inputs.lowpass_noise(T, seed=2), dtype=torch.float64, device="cuda")
+    w = torch.tensor(inputs.rng(5).standard_normal(T + 1), dtype=torch.float64, device="cuda")
+    plan = R.Plan(0.0, 1.0, a, nx, dt, N, ov, dtype=F64)
+    plan.run_keep(g1, None, T, j_r=jr)
+    got = plan.adjoint(g2, None, T, jr, w, want_a=True)
+    o = oracle_mod.adjoint(nx, T, a, dt, host(g2), np.zeros(T + 1), jr, host(w))
+    assert abs(float(got["grad_a"][0]) - o["da"]) <= 1e-12 * o["abs_da"]
+    # a changed span discards the kept states as well
+    plan.run_keep(g1, None, T, j_r=jr)
+    plan.set_span(4)
+    got = plan.adjoint(g1, None, T, jr, w, want_a=True)
+    o = oracle_mod.adjoint(nx, T, a, dt, host(g1), np.zeros(T + 1), jr, host(w))
+    assert abs(float(got["grad_a"][0]) - o["da"]) <= 1e-12 * o["abs_da"]
+    assert_bitwise(host(got["grad_fA"]), o["dg"], "grad_fA")
