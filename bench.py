@@ -58,6 +58,7 @@ def load_peaks() -> dict:
         return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
+NO_TRACES = False  # profiling case without interface traces (--no-traces)
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_span_kernel_c2.md")
 # the sources of the span kernels a run without point sources executes
 KERNEL_SOURCES = ["span_kernel.cuh", "span_kernel.cu", "span_common.cuh", "rswr_device.cuh", "rswr_internal.h"]
@@ -143,7 +144,8 @@ def measure_alu(torch, dev) -> dict:
     clocks = ClockSampler(gpu_uuid(torch, dev))
     clocks.start()
     time.sleep(0.3)
-    res = {name: rswr.fma_rate(dt, device=dev) for name, dt in (("f64", rswr.F64), ("f32", rswr.F32))}
+    res = {name: rswr.fma_rate(dt, device=dev) for name, dt in (("f64", rswr.F64), ("f32", rswr.F32),
+                                                                ("f32x2", 2), ("f32x2_add", 3))}
     clk = clocks.stop()
     mhz = clk["sm_mhz"] if clk else SM_MAX_MHZ
     for r in res.values():
@@ -592,10 +594,10 @@ def profile_case(which: str, variant=None, span=None, full=False, log2_nx=22) ->
     if variant is not None:
         plan.set_variant(variant)
     for _ in range(2):
-        plan.run(p.fA, p.fB, p.T, traces=True)
+        plan.run(p.fA, p.fB, p.T, traces=not NO_TRACES)
     torch.cuda.synchronize()
     plan.check()
-    print(json.dumps({"profile_case": which, "nx": p.nx, "T": p.T, "info": plan.info()}))
+    print(json.dumps({"profile_case": which, "nx": p.nx, "T": p.T, "traces": not NO_TRACES, "info": plan.info()}))
 
 
 # ----------------------------------------------------------------------------
@@ -983,11 +985,14 @@ def main():
                          "adj64/adj32: default 20 = the c4 grid)")
     ap.add_argument("--span", type=int, default=None, help="steps per span of the profiling case")
     ap.add_argument("--full", action="store_true", help="profiling case at the bench's full size")
+    ap.add_argument("--no-traces", action="store_true", help="profiling case without the interface traces")
     ap.add_argument("--peaks", action="store_true",
                     help="measure the FP64 / FP32 pipe rates with the library's FMA probe kernel and exit")
     args = ap.parse_args()
 
     if args.profile_case:
+        global NO_TRACES
+        NO_TRACES = args.no_traces
         lg = args.profile_log2_nx
         if lg is None:
             lg = 20 if args.profile_case in ("adj64", "adj32") else 22
@@ -1017,6 +1022,8 @@ def main():
                           "f64_fma_per_s": m["f64"]["fma_per_s"], "f32_fma_per_s": m["f32"]["fma_per_s"],
                           "f64_per_sm_per_clock": m["f64"]["per_sm_per_clock"],
                           "f32_per_sm_per_clock": m["f32"]["per_sm_per_clock"],
+                          "f32x2_lanes_per_sm_per_clock": m["f32x2"]["per_sm_per_clock"],
+                          "f32x2_add_lanes_per_sm_per_clock": m["f32x2_add"]["per_sm_per_clock"],
                           "f64_glups_at_3_instr": m["f64"]["fma_per_s"] / 3 / 1e9,
                           "f32_glups_at_4_instr": m["f32"]["fma_per_s"] / 4 / 1e9,
                           "detail": m}), flush=True)

@@ -414,10 +414,13 @@ rswr_status rswr_run_noalloc(double xa, double xb, double a, int64_t nx, double 
  * denominator of the span kernels' roofline.  Launches `blocks` x `threads`
  * threads (threads a multiple of 32, at most 1024) on `stream`; each thread
  * runs 8 independent chains of `iters` fused multiply-adds of `dtype`
- * (RSWR_F64: the FP64 pipe, RSWR_F32: the FP32 pipe) and writes one value to
- * sink[thread] (device, blocks * threads elements of dtype, caller-owned).
- * The call is asynchronous and changes no device setting; the caller times it
- * with events on `stream`: rate = 8 * iters * blocks * threads / seconds.
+ * (RSWR_F64: the FP64 pipe, RSWR_F32: the FP32 pipe; 2: packed pairs of FP32
+ * values, fma.rn.f32x2, two FMA lanes per instruction; 3: packed adds,
+ * add.rn.f32x2) and writes one value
+ * to sink[thread] (device, blocks * threads elements of FP64 for RSWR_F64,
+ * else FP32, caller-owned).  The call is asynchronous and changes no device
+ * setting; the caller times it with events on `stream`: FMA lanes per second
+ * = 8 * iters * blocks * threads / seconds (twice that for dtypes 2, 3).
  * Errors: EINVAL (bad sizes, NULL sink, dtype), ECUDA (launch failed).
  */
 rswr_status rswr_fma_probe(int32_t dtype, int64_t iters, int32_t blocks, int32_t threads, void* sink, void* stream);
@@ -440,6 +443,24 @@ rswr_status rswr_variant_get(int32_t v, int32_t* dtype, int32_t* form, int32_t* 
  * Any pointer may be NULL.  RSWR_EINVAL for v out of range. */
 rswr_status rswr_variant_get_tiling(int32_t v, int32_t* warp_halo, int32_t* window, int32_t* max_span,
                                     int32_t* threads_launched);
+
+/* How a variant runs its CTAs (*kind):
+ *   RSWR_VARIANT_SINGLE_ROLE      every thread loads, steps and stores windows;
+ *   RSWR_VARIANT_WARP_SPECIALISED compute warps plus one producer warp that
+ *                                 moves the windows (tickets, TMA, flags);
+ *   RSWR_VARIANT_RESIDENT         one CTA per tile for the whole run, the
+ *                                 window kept on chip and only halo strips
+ *                                 exchanged between spans; a grid whose tiles
+ *                                 do not all fit on the GPU at once is refused
+ *                                 by rswr_run with RSWR_ENOTSUP (never a
+ *                                 default variant; the autotuner tries it).
+ * RSWR_EINVAL for v out of range or kind NULL. */
+typedef enum {
+    RSWR_VARIANT_SINGLE_ROLE = 0,
+    RSWR_VARIANT_WARP_SPECIALISED = 1,
+    RSWR_VARIANT_RESIDENT = 2
+} rswr_variant_kind;
+rswr_status rswr_variant_get_kind(int32_t v, int32_t* kind);
 
 #ifdef __cplusplus
 }

@@ -130,7 +130,7 @@ rswr_status run_noalloc(const rswr_problem& q, int form, const void* fA, const v
     int v = -1;
     for (int i = 0; i < span_variant_count(); ++i) {
         const VariantInfo vi = span_variant_info(i);
-        if (vi.dtype == dtype && vi.form == form && (vi.max_span == 0 || S <= vi.max_span)) {
+        if (vi.dtype == dtype && vi.form == form && !vi.resident && (vi.max_span == 0 || S <= vi.max_span)) {
             v = i;
             break;
         }

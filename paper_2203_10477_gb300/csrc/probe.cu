@@ -46,6 +46,40 @@ __global__ void fma_probe_kernel(Real a, Real b, int64_t iters, Real* sink)
     sink[tid] = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
 }
 
+// The same with packed pairs of FP32 values (fma.rn.f32x2, or add.rn.f32x2
+// when ADD): 16 FP32 lanes per iteration in 8 instructions.
+template <bool ADD>
+__global__ void fma2_probe_kernel(float a, float b, int64_t iters, float* sink)
+{
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t x[8], ab, bb;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ab) : "f"(a), "f"(a));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(bb) : "f"(b), "f"(b));
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float lo = (float)threadIdx.x * 1e-3f + (float)c, hi = lo + 0.5f;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(x[c]) : "f"(lo), "f"(hi));
+    }
+#pragma unroll 16
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            if constexpr (ADD)
+                asm("add.rn.f32x2 %0, %0, %1;" : "+l"(x[c]) : "l"(bb));
+            else
+                asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x[c]) : "l"(ab), "l"(bb));
+        }
+    }
+    float acc = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        float lo, hi;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x[c]));
+        acc += lo + hi;
+    }
+    sink[tid] = acc;
+}
+
 }  // namespace
 
 extern "C" rswr_status rswr_fma_probe(int32_t dtype, int64_t iters, int32_t blocks, int32_t threads, void* sink,
@@ -61,8 +95,12 @@ extern "C" rswr_status rswr_fma_probe(int32_t dtype, int64_t iters, int32_t bloc
         fma_probe_kernel<double><<<blocks, threads, 0, s>>>(0.999999, 1e-7, iters, static_cast<double*>(sink));
     else if (dtype == RSWR_F32)
         fma_probe_kernel<float><<<blocks, threads, 0, s>>>(0.999999f, 1e-7f, iters, static_cast<float*>(sink));
+    else if (dtype == 2)
+        fma2_probe_kernel<false><<<blocks, threads, 0, s>>>(0.999999f, 1e-7f, iters, static_cast<float*>(sink));
+    else if (dtype == 3)
+        fma2_probe_kernel<true><<<blocks, threads, 0, s>>>(0.999999f, 1e-7f, iters, static_cast<float*>(sink));
     else {
-        set_error_message("rswr_fma_probe: dtype must be RSWR_F32 or RSWR_F64");
+        set_error_message("rswr_fma_probe: dtype must be RSWR_F32, RSWR_F64, 2 (packed FP32 pairs) or 3 (packed adds)");
         return RSWR_EINVAL;
     }
     const cudaError_t e = cudaGetLastError();

@@ -109,6 +109,8 @@ struct Engine {
     unsigned long long* d_ticket = nullptr;
     int* d_done = nullptr;
     size_t done_cap = 0;
+    void* d_xbuf = nullptr;  // resident variants: halo strips of every tile
+    size_t xbuf_cap = 0;     // bytes
     DevError* d_err = nullptr;
     void* d_host_stage = nullptr;  // rswr_run_host staging
     size_t host_stage_cap = 0;
@@ -174,6 +176,7 @@ void free_engine(Engine* e)
     cudaFree(e->d_offsets);
     cudaFree(e->d_ticket);
     cudaFree(e->d_done);
+    cudaFree(e->d_xbuf);
     cudaFree(e->d_err);
     cudaFree(e->d_host_stage);
     cudaFree(e->adj_mem);
@@ -187,9 +190,10 @@ bool variant_takes_span(const VariantInfo& vi, int S) { return vi.max_span == 0 
 int default_variant(int dtype, int form, int S)
 {
     // first registered variant of the dtype/form that runs spans of S steps
+    // (resident variants fit small grids only: chosen by the autotuner or the caller)
     for (int v = 0; v < span_variant_count(); ++v) {
         const VariantInfo vi = span_variant_info(v);
-        if (vi.dtype == dtype && vi.form == form && variant_takes_span(vi, S)) return v;
+        if (vi.dtype == dtype && vi.form == form && !vi.resident && variant_takes_span(vi, S)) return v;
     }
     return -1;
 }
@@ -271,6 +275,16 @@ rswr_status layout(Engine* e)
     }
     RSWR_CUDA(cudaMemcpy(e->d_offsets, e->h_offsets.data(), sizeof(int64_t) * e->h_offsets.size(),
                          cudaMemcpyHostToDevice));
+    if (vi.resident) {
+        const size_t xb = es * 8 * (size_t)e->H * (size_t)e->ntiles;
+        if (xb > e->xbuf_cap) {
+            cudaFree(e->d_xbuf);
+            e->d_xbuf = nullptr;
+            e->xbuf_cap = 0;
+            if (cudaMalloc(&e->d_xbuf, xb) != cudaSuccess) return fail(RSWR_ENOMEM, "halo exchange slots");
+            e->xbuf_cap = xb;
+        }
+    }
     return RSWR_OK;
 }
 
@@ -611,6 +625,7 @@ SpanParams<Real> span_params(Engine* e, int64_t T, int nspans)
     prm.inject_span = e->inject_span;
     prm.ticket = e->d_ticket;
     prm.done = e->d_done;
+    prm.xbuf = static_cast<Real*>(e->d_xbuf);
     prm.err = e->d_err;
     prm.wait_ns = (long long)(e->wait_s * 1e9);
     return prm;
@@ -665,7 +680,14 @@ rswr_status device_work(Engine* e, const RunReq& r, int nprobe, int64_t mono_blk
         RSWR_CUDA(span_occupancy(e->variant, &bps));
         if (bps < 1) return fail(RSWR_ENOTSUP, "span kernel does not fit on an SM");
         if (nspans > 0) {
-            if (e->mode == RSWR_MODE_PERSISTENT) {
+            if (span_variant_info(e->variant).resident) {
+                // one CTA per tile for the whole run: every tile must be resident at once
+                if ((int64_t)bps * e->num_sms < e->ntiles)
+                    return fail(RSWR_ENOTSUP, "resident variant: " + std::to_string(e->ntiles) +
+                                                  " tiles do not fit on the GPU at once");
+                RSWR_CUDA(cudaMemsetAsync(e->d_done, 0, sizeof(int) * e->ntiles, s));
+                RSWR_CUDA(span_launch(e->variant, &prm, (int)e->ntiles, s));
+            } else if (e->mode == RSWR_MODE_PERSISTENT) {
                 RSWR_CUDA(cudaMemsetAsync(e->d_ticket, 0, sizeof(unsigned long long), s));
                 RSWR_CUDA(cudaMemsetAsync(e->d_done, 0, sizeof(int) * e->ntiles, s));
                 const int grid = (int)std::min<int64_t>((int64_t)bps * e->num_sms, (int64_t)nspans * e->ntiles);
@@ -790,7 +812,8 @@ rswr_status run_impl(Engine* e, const RunReq& r, cudaStream_t s)
     int64_t mono_blk_off = -1;
     rswr_status st = prepare_tables<Real>(e, r, &nprobe, &mono_blk_off, s);
     if (st != RSWR_OK) return st;
-    if (e->use_graph) return run_graph<Real>(e, r, nprobe, mono_blk_off, s);
+    // resident variants launch cooperatively: directly, not from a captured graph
+    if (e->use_graph && !span_variant_info(e->variant).resident) return run_graph<Real>(e, r, nprobe, mono_blk_off, s);
     return device_work<Real>(e, r, nprobe, mono_blk_off, s);
 }
 
@@ -1010,7 +1033,10 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     const VariantInfo ai = adj_variant_info(va);
     const int SA = std::min(e->S, adj_variant_span(va));
     const int H = (SA + 3) / 4 * 4;
-    const int vf = e->variant;
+    // the sweeps launch span by span or with tickets: a resident plan variant
+    // gives way to the default one of its dtype and form
+    const int vf = span_variant_info(e->variant).resident ? default_variant(e->dtype, e->form, SA) : e->variant;
+    if (vf < 0) return fail(RSWR_ENOTSUP, "no span kernel variant for the adjoint sweep");
     const VariantInfo fi = span_variant_info(vf);
     const int core_f = fi.W - 2 * H;
     const int64_t pad = H + 8;
@@ -1503,7 +1529,7 @@ rswr_status autotune_engine(Engine* e, int64_t probe_steps, int32_t* variant, cu
         const VariantInfo vi = span_variant_info(v);
         if (vi.dtype != e->dtype || vi.form != e->form) continue;
         for (int S : spans) {
-            for (int mode = 0; mode < 2; ++mode) {
+            for (int mode = 0; mode < (vi.resident ? 1 : 2); ++mode) {
                 if (apply_choice(e, TuneChoice{v, mode, S}) != RSWR_OK) continue;
                 if (run_engine(e, r, s) != RSWR_OK) continue;  // warm-up (and graph capture)
                 RSWR_CUDA(cudaEventRecord(a, s));
@@ -2138,6 +2164,16 @@ rswr_status rswr_variant_get(int32_t v, int32_t* dtype, int32_t* form, int32_t* 
     if (form) *form = vi.form == kCanonical ? RSWR_FORM_CANONICAL : RSWR_FORM_INCREMENT;
     if (points_per_thread) *points_per_thread = vi.P;
     if (threads_per_cta) *threads_per_cta = vi.NT;
+    return RSWR_OK;
+}
+
+rswr_status rswr_variant_get_kind(int32_t v, int32_t* kind)
+{
+    if (v < 0 || v >= span_variant_count()) return fail(RSWR_EINVAL, "variant out of range");
+    if (!kind) return fail(RSWR_EINVAL, "kind is NULL");
+    const VariantInfo vi = span_variant_info(v);
+    *kind = vi.resident ? RSWR_VARIANT_RESIDENT : (vi.threads > vi.NT ? RSWR_VARIANT_WARP_SPECIALISED
+                                                                     : RSWR_VARIANT_SINGLE_ROLE);
     return RSWR_OK;
 }
 

@@ -87,6 +87,7 @@ struct SpanParams {
     int64_t ck_stride;           // 0: span k reads q[k & 1] and writes q[(k + 1) & 1];
                                  // > 0: span k reads q[0] + k * ck_stride and writes
                                  // q[0] + (k + 1) * ck_stride (every span state kept)
+    Real* xbuf;                  // resident variants: halo strips, [tile][span parity][side][component][H]
 };
 
 template <typename Real>
@@ -179,6 +180,7 @@ struct VariantInfo {
     int W;   // points per CTA window
     int threads;   // threads per CTA at launch (NT, or NT + a producer warp)
     int max_span;  // longest span the variant runs (0: any that fits the window)
+    int resident;  // 1: one CTA per tile for the whole run (cooperative launch, grid = tiles)
 };
 
 // span_kernel.cu

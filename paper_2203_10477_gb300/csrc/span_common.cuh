@@ -183,6 +183,29 @@ __device__ __forceinline__ void reg_apply(int r, F&& f)
     }
 }
 
+// f(I) on register I = r through a switch (a jump table: one indirect branch
+// instead of a tree of compares, which the compiler may turn into predicated
+// code that every lane executes); registers 1 .. P-2 only, P <= 32.
+template <int P, typename F>
+__device__ __forceinline__ void reg_switch(int r, F&& f)
+{
+    static_assert(P <= 32, "reg_switch covers 32 registers");
+#define RSWR_CASE(i)                                                     \
+    case i:                                                              \
+        if constexpr (i > 0 && i < P - 1) f(std::integral_constant<int, i>{}); \
+        break;
+    switch (r) {
+        RSWR_CASE(1) RSWR_CASE(2) RSWR_CASE(3) RSWR_CASE(4) RSWR_CASE(5) RSWR_CASE(6) RSWR_CASE(7) RSWR_CASE(8)
+        RSWR_CASE(9) RSWR_CASE(10) RSWR_CASE(11) RSWR_CASE(12) RSWR_CASE(13) RSWR_CASE(14) RSWR_CASE(15)
+        RSWR_CASE(16) RSWR_CASE(17) RSWR_CASE(18) RSWR_CASE(19) RSWR_CASE(20) RSWR_CASE(21) RSWR_CASE(22)
+        RSWR_CASE(23) RSWR_CASE(24) RSWR_CASE(25) RSWR_CASE(26) RSWR_CASE(27) RSWR_CASE(28) RSWR_CASE(29)
+        RSWR_CASE(30)
+        default:
+            break;
+    }
+#undef RSWR_CASE
+}
+
 template <typename Real, int P>
 __device__ __forceinline__ Real reg_get(const Real (&u)[P], int r)
 {
@@ -528,15 +551,30 @@ struct NoRecord {
     __device__ __forceinline__ void operator()(const U&, Real, Real, int) const {}
 };
 
-template <typename Real, int FORM, int P, typename Rec = NoRecord>
+// Special points in the edges-first loop (Dirichlet nodes, a point source, the
+// outside points next to the nodes; see patch_special): pre(u, s) runs before
+// step s (samples, level-n values), edges(u, n0, v0, nl, vl) patches the new
+// values of the thread's first and last register before they are shuffled,
+// interior(u, w) the registers in between after their update.
+struct NoPatch {
+    template <typename U>
+    __device__ __forceinline__ void pre(const U&, int) {}
+    template <typename U, typename Real>
+    __device__ __forceinline__ void edges(const U&, Real&, Real&, Real&, Real&) {}
+    template <typename U>
+    __device__ __forceinline__ void interior(U&, U&) {}
+};
+
+template <typename Real, int FORM, int P, typename Rec = NoRecord, typename Patch = NoPatch>
 __device__ __forceinline__ void warp_steps_edges_first(Real (&u)[P], Real (&w)[P], Real c2, Real k, int steps,
-                                                       int lane, Rec rec = Rec{})
+                                                       int lane, Rec rec = Rec{}, Patch patch = Patch{})
 {
     static_assert(P >= 3, "edges-first order needs interior points");
     Real lft, rgt;
     warp_neighbours<Real, P>(u, lft, rgt, lane);
     for (int s = 0; s < steps; ++s) {
         rec(u, lft, rgt, s);
+        patch.pre(u, s);
         Real n0, nl, v0, vl;  // new first / last point and their second components
         Real d0 = Real(0);
         if constexpr (FORM == kIncrement) {
@@ -552,6 +590,7 @@ __device__ __forceinline__ void warp_steps_edges_first(Real (&u)[P], Real (&w)[P
             nl = rfma(c2, radd(u[P - 2], rgt), rfma(k, u[P - 1], -w[P - 1]));
             vl = u[P - 1];
         }
+        patch.edges(u, n0, v0, nl, vl);
         Real nlft = __shfl_up_sync(kFull, nl, 1);
         Real nrgt = __shfl_down_sync(kFull, n0, 1);
         if constexpr (FORM == kIncrement) {
@@ -579,12 +618,126 @@ __device__ __forceinline__ void warp_steps_edges_first(Real (&u)[P], Real (&w)[P
         w[0] = v0;
         u[P - 1] = nl;
         w[P - 1] = vl;
+        patch.interior(u, w);
         if (lane == 0) nlft = u[1];
         if (lane == 31) nrgt = u[P - 2];
         lft = nlft;
         rgt = nrgt;
     }
 }
+
+// The patch of the special points for warp_steps_edges_first, with the same
+// effect as leap_step + patch_special: a register takes, in this order, the
+// source (canonical u' += s; increment v' += s, u' = u_old + v'), the left node
+// (u' = f_A(n+1); increment v' = f_A(n+1) - f_A(n)), the outside point next to
+// it (0, 0), the right node, the outside point next to it.  Samples come from
+// the warp's chunks (f_A / f_B at level n0 + d, the source at level n0 + d + 1).
+// Whether a special point of the thread sits between its first and last
+// register (the register trees of EdgePatch::interior are needed).
+template <int P>
+__device__ __forceinline__ bool interior_special(const Special& sp)
+{
+    auto in = [](int r) { return r > 0 && r < P - 1; };
+    return in(sp.rs) || in(sp.r0) || in(sp.rm) || in(sp.r1) || in(sp.rp);
+}
+
+// INTERIOR = false: every special point of the warp sits on a thread's first
+// or last register, so interior() has nothing to do and is compiled out (the
+// register trees, which the compiler turns into predicated code that every lane
+// executes each step, are what make the patched loop slow).
+template <typename Real, int FORM, int P, typename Reload, bool INTERIOR = true>
+struct EdgePatch {
+    Special sp;
+    WarpChunk<Real>* ca;
+    WarpChunk<Real>* cb;
+    WarpChunk<Real>* cs;
+    bool wa, wb, wsrc;
+    int* cbase;       // first step of the current chunk
+    Reload* reload;   // reload(first): loads the chunk after the one starting at `first`
+    Real fa_old, fa_new, fb_old, fb_new, sval, uold_s;
+    int d;
+
+    template <typename U>
+    __device__ __forceinline__ void pre(const U& u, int s)
+    {
+        step_samples(s);
+        capture(u);
+    }
+    __device__ __forceinline__ void step_samples(int s)
+    {
+        d = s - *cbase;
+        if (d == 32) {
+            *cbase += 32;
+            ca->c0 = ca->c1;
+            cb->c0 = cb->c1;
+            cs->c0 = cs->c1;
+            (*reload)(*cbase, false);
+            d = 0;
+        }
+        fa_old = fa_new = fb_old = fb_new = sval = Real(0);
+        if (wsrc) sval = cs->get(d);
+        if (wa) {
+            fa_old = ca->get(d);
+            fa_new = ca->get(d + 1);
+        }
+        if (wb) {
+            fb_old = cb->get(d);
+            fb_new = cb->get(d + 1);
+        }
+    }
+    __device__ __forceinline__ void at(int i, Real& x, Real& y)
+    {
+        if (sp.rs == i) {
+            if constexpr (FORM == kIncrement) {
+                y = radd(y, sval);
+                x = radd(uold_s, y);
+            } else {
+                x = radd(x, sval);
+            }
+        }
+        if (sp.r0 == i) {
+            x = fa_new;
+            if constexpr (FORM == kIncrement) y = rsub(fa_new, fa_old);
+        }
+        if (sp.rm == i) x = y = Real(0);
+        if (sp.r1 == i) {
+            x = fb_new;
+            if constexpr (FORM == kIncrement) y = rsub(fb_new, fb_old);
+        }
+        if (sp.rp == i) x = y = Real(0);
+    }
+    template <typename U>
+    __device__ __forceinline__ void capture(const U& u)
+    {
+        // the level-n value of the source point (increment form)
+        if constexpr (FORM == kIncrement)
+            if (sp.rs >= 0) uold_s = reg_get<Real, P>(u, sp.rs);
+    }
+    template <typename U>
+    __device__ __forceinline__ void edges(const U& u, Real& n0, Real& v0, Real& nl, Real& vl)
+    {
+        at(0, n0, v0);
+        at(P - 1, nl, vl);
+    }
+    template <typename U>
+    __device__ __forceinline__ void interior(U& u, U& w)
+    {
+        if constexpr (!INTERIOR) return;
+        // one jump-table branch per special point held between the end registers
+        auto one = [&](int r) {
+            if (r > 0 && r < P - 1)
+                reg_switch<P>(r, [&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    at(i, u[i], w[i]);
+                });
+        };
+        one(sp.rs);
+        if (sp.r0 != sp.rs) one(sp.r0);
+        one(sp.rm);
+        if (sp.r1 != sp.rs) one(sp.r1);
+        one(sp.rp);
+    }
+};
 
 // Write the registers a thread owns, [own_lo, own_hi), back to the shared window.
 template <typename Real, int P, int KH>

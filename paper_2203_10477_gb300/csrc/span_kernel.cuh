@@ -277,6 +277,42 @@ __device__ __forceinline__ void predict_tile(const SpanParams<Real>& prm, const 
             wsrc = __any_sync(kFull, sp.rs >= 0);
             reload(0, true);
         }
+        // the probe recording of the edges-first loops: each level recorded by its
+        // owner before it is advanced
+        auto recf = [&](const Real(&uu)[P], Real l, Real r, int s) {
+            if (nown > 0) record_step<Real, P>(op0, uu, l, r, s);
+            if (nown > 1) record_step<Real, P>(op1, uu, l, r, s);
+            for (uint32_t m = more; m != 0u; m &= m - 1u)
+                record_owned<Real, P>(uu, l, r, tprobes[__ffs(m) - 1], wabs, tb, n0 + s_begin + s);
+        };
+        if constexpr (KH > 0 && SP && !US) {
+            // free / refreshed warp windows of an edge or source tile: the warp's
+            // choice (uniform across its lanes); a warp without special points
+            // runs the bare (or recording) loop, one with them the edges-first
+            // loop with the points patched
+            if (!many_probes) {
+                const bool wsp = __any_sync(kFull, any_special(sp));
+                const bool wpr = PR && __any_sync(kFull, nown > 0);
+                if (!wsp) {
+                    if (wpr) warp_steps_edges_first<Real, FORM, P>(u, w, c2, kk, s_end - s_begin, lane, recf);
+                    else warp_steps_edges_first<Real, FORM, P>(u, w, c2, kk, s_end - s_begin, lane);
+                    return;
+                }
+                auto steps_with = [&](auto ep) {
+                    if (wpr)
+                        warp_steps_edges_first<Real, FORM, P>(u, w, c2, kk, s_end - s_begin, lane, recf, ep);
+                    else
+                        warp_steps_edges_first<Real, FORM, P>(u, w, c2, kk, s_end - s_begin, lane, NoRecord{}, ep);
+                };
+                if (__any_sync(kFull, interior_special<P>(sp)))
+                    steps_with(EdgePatch<Real, FORM, P, decltype(reload), true>{sp, &ca, &cb, &cs, wa, wb, wsrc,
+                                                                                 &cbase, &reload});
+                else
+                    steps_with(EdgePatch<Real, FORM, P, decltype(reload), false>{sp, &ca, &cb, &cs, wa, wb, wsrc,
+                                                                                  &cbase, &reload});
+                return;
+            }
+        }
         if constexpr (KH > 0 && !SP) {
             if constexpr (!PR) {
                 // plain interior tile of a warp window: the bare stencil, edges first
@@ -284,15 +320,14 @@ __device__ __forceinline__ void predict_tile(const SpanParams<Real>& prm, const 
                 return;
             } else {
                 // interior tile with probes: edges first as well, each level
-                // recorded by its owner before it is advanced
+                // recorded by its owner before it is advanced; a warp that owns
+                // none of the tile's probes runs the bare stencil (warp-uniform)
+                if (!many_probes && !__any_sync(kFull, nown > 0)) {
+                    warp_steps_edges_first<Real, FORM, P>(u, w, c2, kk, s_end - s_begin, lane);
+                    return;
+                }
                 if (!many_probes) {
-                    warp_steps_edges_first<Real, FORM, P>(
-                        u, w, c2, kk, s_end - s_begin, lane, [&](const Real(&uu)[P], Real l, Real r, int s) {
-                            if (nown > 0) record_step<Real, P>(op0, uu, l, r, s);
-                            if (nown > 1) record_step<Real, P>(op1, uu, l, r, s);
-                            for (uint32_t m = more; m != 0u; m &= m - 1u)
-                                record_owned<Real, P>(uu, l, r, tprobes[__ffs(m) - 1], wabs, tb, n0 + s_begin + s);
-                        });
+                    warp_steps_edges_first<Real, FORM, P>(u, w, c2, kk, s_end - s_begin, lane, recf);
                     return;
                 }
             }
@@ -868,10 +903,147 @@ __global__ void __launch_bounds__(NT + 32, MINB) span_kernel_ws(const __grid_con
     }
 }
 
+// ---- resident tiles: one CTA keeps its tile for the whole run ----------------
+// On a grid whose tiles all fit on the GPU at once (a cooperative launch of
+// one CTA per tile) a span is about one wave of tiles, and reloading every
+// window through global memory each span puts a load, the S steps, a store
+// and a flag round trip on the critical path of every span.  Here each CTA
+// keeps its window in shared memory and registers for all spans; after a span
+// only the H core points next to each window end (both components) go
+// through global memory: written to a double-buffered exchange slot, a
+// release flag per tile, a bounded acquire wait for the two neighbours, and
+// their strips become this window's halos.  The points outside the grid stay
+// 0 (as in the reloading kernels, whose halo loads read the zero pads).  The
+// select is the same index range, so the result is the same bit for bit.
+template <typename Real>
+__device__ bool wait_neighbours(const SpanParams<Real>& prm, int tile, bool left, bool right, int target, int k)
+{
+    auto ready = [&]() {
+        return (!left || ld_acquire(prm.done + tile - 1) >= target) &&
+               (!right || ld_acquire(prm.done + tile + 1) >= target);
+    };
+    if (ready()) return true;
+    const long long t0 = global_ns();
+    unsigned ns = 32;
+    for (;;) {
+        __nanosleep(ns);
+        if (ns < 64) ns <<= 1;
+        if (ready()) return true;
+        if (*(volatile int*)&prm.err->code != 0) return false;
+        if (global_ns() - t0 > prm.wait_ns) {
+            latch_error(prm.err, kDevTimeoutFlag, tile, k, 0);
+            return false;
+        }
+    }
+}
+
+template <typename Real, int FORM, int P, int NT, int KH, int MINB, bool USRC>
+__global__ void __launch_bounds__(NT, MINB) span_kernel_res(const __grid_constant__ SpanParams<Real> prm)
+{
+    using G = Geom<P, NT, KH>;
+    constexpr int W = G::W;
+    constexpr int NW = G::NW;
+    static_assert(W % 4 == 0, "windows must span whole 16-byte units");
+    static_assert(KH == 0 || G::FREE || P >= 2 * KH, "this kernel refreshes warp halos");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Real* su = reinterpret_cast<Real*>(smem_raw);  // [2 components][W]: one stage
+    Real* sw = su + W;
+    Real* xch = su + 2 * W;
+    Real* hx = xch + ((4 * NW + 15) / 16) * 16;
+    __shared__ __align__(8) uint64_t full_bar;
+    __shared__ ProbeDev<Real> s_probes[kTileProbes];
+    __shared__ int s_ok;
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int tile = blockIdx.x;
+    const TileDev td = prm.tiles[tile];
+    const ProblemDev<Real>& pr = prm.problems[td.problem];
+    const int H = prm.H;
+    const int64_t gj0 = (int64_t)td.local * prm.core - H;
+    const bool edge = (gj0 <= 0) || (gj0 + W - 1 >= pr.nx - 1);
+    const bool left = td.local > 0;
+    const bool right = td.local + 1 < pr.ntiles;
+    const int tb = warp * G::CW + lane * P;
+    int own_lo, own_hi;
+    owned_range<P, NW, KH>(warp, lane, own_lo, own_hi);
+    const int np = td.probe_end - td.probe_begin;
+    if (np > 0 && np <= kTileProbes && tid < np) s_probes[tid] = prm.probes[td.probe_begin + tid];
+
+    // the window at level 0
+    if (tid == 0) {
+        mbar_init(&full_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async_smem();
+        issue_load<Real, W>(prm, (long long)tile, su, &full_bar);
+    }
+    __syncthreads();
+    {
+        const bool ok = mbar_wait_bounded(&full_bar, 0u, prm.wait_ns, &prm.err->code);
+        if (!ok) latch_error(prm.err, kDevTimeoutLoad, tile, 0, 0);
+        if (__syncthreads_or(!ok)) return;
+    }
+
+    for (int k = 0; k < prm.nspans; ++k) {
+        const int64_t n0 = (int64_t)k * prm.S;
+        const int steps = (int)((prm.T - n0 < prm.S) ? (prm.T - n0) : prm.S);
+        Real u[P], w[P];
+        smem_to_regs<Real, P>(su + tb, u);
+        smem_to_regs<Real, P>(sw + tb, w);
+        predict_tile<Real, FORM, P, NW, KH, 0, USRC>(prm, pr, td, u, w, gj0, n0, steps, tb, own_lo, own_hi, s_probes,
+                                                  np, xch, hx, warp, lane, edge);
+        __syncthreads();  // every window is read (KH > 0: they overlap) before owned points are written back
+        owned_to_smem<Real, P, KH>(su + tb, u, own_lo, own_hi);
+        owned_to_smem<Real, P, KH>(sw + tb, w, own_lo, own_hi);
+        __syncthreads();
+        if (k + 1 == prm.nspans) break;
+
+        // strips out: the first and last H core points, both components
+        const int par = k & 1;
+        Real* xb = prm.xbuf;
+        for (int i = tid; i < 4 * H; i += NT) {
+            const int side = i / (2 * H), comp = (i / H) & 1, j = i % H;
+            const Real* src = (comp ? sw : su) + (side ? W - 2 * H : H) + j;
+            xb[((((int64_t)tile * 2 + par) * 2 + side) * 2 + comp) * H + j] = *src;
+        }
+        // the CTA barrier orders every thread's strip stores before thread 0's
+        // gpu-scope release of the flag, and a release is cumulative: a
+        // neighbour that acquires the flag sees the strips
+        __syncthreads();
+        if (tid == 0) {
+            // (test hook: the injected tile stops publishing from that span on, so
+            // its neighbours' bounded waits expire)
+            if (!(tile == prm.inject_tile && k >= prm.inject_span)) st_release(prm.done + tile, k + 1);
+            s_ok = wait_neighbours(prm, tile, left, right, k + 1, k) ? 1 : 0;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        // halos in: the left neighbour's last core points, the right neighbour's first ones (L2 reads)
+        for (int i = tid; i < 4 * H; i += NT) {
+            const int side = i / (2 * H), comp = (i / H) & 1, j = i % H;
+            if (side == 0 && left)
+                (comp ? sw : su)[j] = __ldcg(xb + ((((int64_t)(tile - 1) * 2 + par) * 2 + 1) * 2 + comp) * H + j);
+            if (side == 1 && right)
+                (comp ? sw : su)[W - H + j] = __ldcg(xb + ((((int64_t)(tile + 1) * 2 + par) * 2 + 0) * 2 + comp) * H + j);
+        }
+        __syncthreads();
+    }
+    // the final level: the core into the state array of the last span
+    const int64_t dst = pr.base + (int64_t)td.local * prm.core;
+    Real* d0 = span_state(prm, 0, prm.nspans) + dst;
+    Real* d1 = span_state(prm, 1, prm.nspans) + dst;
+    for (int i = tid; i < prm.core; i += NT) {
+        d0[i] = su[H + i];
+        d1[i] = sw[H + i];
+    }
+}
+
 }  // namespace rswr
 
 // The registered variants, in variant-index order: WS = warp-specialised
-// (NT compute threads + one producer warp), PLAIN = single-role CTA.
+// (NT compute threads + one producer warp), PLAIN = single-role CTA, RES =
+// resident tiles (one CTA per tile for the whole run; small grids only).
 // Arguments: kind, Real, form, P (points per thread), NT (compute threads),
 // KH (warp halo; 0: warps exchange neighbours every step), MINB (CTAs per SM
 // the register allocation must allow).  The first variant of each dtype/form
@@ -895,7 +1067,10 @@ __global__ void __launch_bounds__(NT + 32, MINB) span_kernel_ws(const __grid_con
     X(WS, double, kCanonical, 8, 256, 0, 2)            \
     X(PLAIN, double, kCanonical, 8, 128, 0, 4)         \
     X(PLAIN, double, kCanonical, 8, 256, 0, 2)         \
-    X(PLAIN, double, kIncrement, 8, 256, 0, 2)
+    X(PLAIN, double, kIncrement, 8, 256, 0, 2)         \
+    X(RES, float, kIncrement, 28, 128, 32, 4)          \
+    X(RES, float, kIncrement, 16, 128, 32, 5)          \
+    X(RES, double, kCanonical, 8, 256, 0, 2)
 
 namespace rswr {
 // span_kernel_src.cu: variant v compiled with user point sources

@@ -20,6 +20,12 @@ const void* src_kernel_WS()
     return reinterpret_cast<const void*>(&span_kernel_ws<Real, FORM, P, NT, KH, MINB, true>);
 }
 
+template <typename Real, int FORM, int P, int NT, int KH, int MINB>
+const void* src_kernel_RES()
+{
+    return reinterpret_cast<const void*>(&span_kernel_res<Real, FORM, P, NT, KH, MINB, true>);
+}
+
 #define RSWR_SRC_KERNEL(kind, Real, FORM, P, NT, KH, MINB) src_kernel_##kind<Real, FORM, P, NT, KH, MINB>(),
 
 }  // namespace

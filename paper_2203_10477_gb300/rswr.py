@@ -105,6 +105,7 @@ SIGNATURES = {
     "rswr_batch_adjoint": (_st, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]),
     "rswr_fma_probe": (_st, [_i32, _i64, _i32, _i32, _vp, _vp]),
     "rswr_variant_count": (_i32, []),
+    "rswr_variant_get_kind": (_st, [_i32, ctypes.POINTER(_i32)]),
     "rswr_variant_get": (_st, [_i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                                ctypes.POINTER(_i32)]),
     "rswr_variant_get_tiling": (_st, [_i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
@@ -203,8 +204,11 @@ def variants() -> list[dict]:
         check(lib().rswr_variant_get(v, ctypes.byref(d), ctypes.byref(f), ctypes.byref(p), ctypes.byref(n)))
         kh, w, ms, th = _i32(), _i32(), _i32(), _i32()
         check(lib().rswr_variant_get_tiling(v, ctypes.byref(kh), ctypes.byref(w), ctypes.byref(ms), ctypes.byref(th)))
+        kind = _i32()
+        check(lib().rswr_variant_get_kind(v, ctypes.byref(kind)))
         out.append({"variant": v, "dtype": d.value, "form": f.value, "P": p.value, "NT": n.value,
-                    "KH": kh.value, "window": w.value, "max_span": ms.value, "threads": th.value})
+                    "KH": kh.value, "window": w.value, "max_span": ms.value, "threads": th.value,
+                    "kind": kind.value, "resident": kind.value == 2})
     return out
 
 
@@ -217,7 +221,7 @@ def fma_rate(dtype, device=None, target_ms=60.0, reps=3) -> dict:
     dev = torch.device("cuda" if device is None else device)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     blocks, threads = 8 * sms, 256
-    td = torch.float64 if dtype == F64 else torch.float32
+    td = torch.float64 if dtype == F64 else torch.float32  # dtypes 2, 3: packed FP32 pairs
     with torch.cuda.device(dev):
         sink = torch.empty(blocks * threads, dtype=td, device=dev)
         stream = torch.cuda.current_stream(dev)
@@ -237,7 +241,7 @@ def fma_rate(dtype, device=None, target_ms=60.0, reps=3) -> dict:
             ms = launch(iters)
         iters = max(1, int(iters * target_ms / ms))
         best = min(launch(iters) for _ in range(reps))
-    fmas = 8.0 * iters * blocks * threads
+    fmas = 8.0 * iters * blocks * threads * (2 if dtype in (2, 3) else 1)
     return {"fma_per_s": fmas / (best / 1e3), "ms": best, "iters": iters, "blocks": blocks, "threads": threads,
             "sms": sms, "finite": bool(torch.isfinite(sink).all())}
 

@@ -538,6 +538,46 @@ def test_missing_flag_times_out_and_context_survives(R, oracle_mod):
     assert_bitwise(host(out["u"])[: len(ref["u"])], ref["u"], "after timeout")
 
 
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_missing_flag_times_out_in_a_resident_variant(R, oracle_mod, dtype):
+    """Resident tiles wait for their neighbours every span: a tile that stops
+    publishing (host-injected) makes the neighbours' bounded waits expire, the
+    run reports RSWR_ETIMEOUT, and a clean run afterwards is exact."""
+    nx, N, ov, T = 50000, 4, 64, 400
+    dt = 0.9 / (nx - 1)
+    fA = inputs.gaussian_pulse(T, dt, sigma_steps=10)
+    plan = R.Plan(0.0, 1.0, 1.0, nx, dt, N, ov, dtype=dtype)
+    res = [v for v in R.variants() if v["dtype"] == dtype and v["form"] == plan.info()["form"] and v["resident"]]
+    assert res, "no resident variant registered"
+    plan.set_variant(res[0]["variant"])
+    assert plan.info()["ntiles"] >= 3
+    plan.set_wait_limit(0.2)
+    plan.inject_missing_flag(1, 3)
+    plan.run(fA, None, T)
+    with pytest.raises(R.RSWRError) as ei:
+        plan.check()
+    assert ei.value.status == 6
+    plan.inject_missing_flag(-1, 0)
+    out = plan.run(fA, None, T)
+    plan.check()
+    form, prec_ = (0, "f64") if dtype == F64 else (1, "f32")
+    ref = oracle_mod.leapfrog(nx, T, 1.0, dt, fA, np.zeros(T + 1), form=form, prec=prec_,
+                              nx_run=oracle_mod.causal_extent(T, nx))
+    assert_bitwise(host(out["u"])[: len(ref["u"])], ref["u"], "after timeout")
+
+
+def test_resident_variant_refuses_a_grid_that_does_not_fit(R):
+    """One CTA per tile for the whole run needs every tile on the GPU at once;
+    a larger grid is refused before anything is launched."""
+    nx = 1 << 24
+    plan = R.Plan(0.0, 1.0, 1.0, nx, 0.9 / (nx - 1), 1024, 64, dtype=F32)
+    res = [v for v in R.variants() if v["dtype"] == F32 and v["form"] == plan.info()["form"] and v["resident"]]
+    plan.set_variant(res[0]["variant"])
+    with pytest.raises(R.RSWRError) as ei:
+        plan.run(np.zeros(11), None, 10)
+    assert ei.value.status == 7  # RSWR_ENOTSUP
+
+
 # ----------------------------------------------------------------------------
 # CUDA graphs, autotuner
 # ----------------------------------------------------------------------------
