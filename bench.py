@@ -662,7 +662,9 @@ def bench_adjoint(torch, dev):
     w = torch.as_tensor(inputs.lowpass_noise(p.T, seed=4), device=dev)
     for name, dtype in (("f64", rswr.F64), ("f32", rswr.F32)):
         plan = rswr.Plan.from_problem(p, dtype=dtype, device=dev)
-        plan.autotune(64)  # variant, mode and span of the sweeps through the span kernel
+        # variant, mode and span of the sweeps through the span kernel, timed on
+        # 16 spans (a few spans would mostly time the start of a launch)
+        plan.autotune(512)
         td = torch.float64 if dtype == rswr.F64 else torch.float32
         fA = torch.as_tensor(p.fA, device=dev).to(td)
         wt = w.to(td)

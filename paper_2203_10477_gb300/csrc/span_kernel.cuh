@@ -174,7 +174,7 @@ struct Geom {
 // the window take it together.  The step loop is instantiated six times
 // (probes yes/no x {plain, special points, special points + user sources}) so
 // that a plain interior tile runs the bare stencil with no per-step tests.
-template <typename Real, int FORM, int P, int NW, int KH, int BAR, bool USRC>
+template <typename Real, int FORM, int P, int NW, int KH, int BAR, bool USRC, bool EDGE_FAST = false>
 __device__ __forceinline__ void predict_tile(const SpanParams<Real>& prm, const ProblemDev<Real>& pr,
                                              const TileDev& td, Real (&u)[P], Real (&w)[P], int64_t gj0, int64_t n0,
                                              int steps, int tb, int own_lo, int own_hi,
@@ -285,7 +285,8 @@ __device__ __forceinline__ void predict_tile(const SpanParams<Real>& prm, const 
             for (uint32_t m = more; m != 0u; m &= m - 1u)
                 record_owned<Real, P>(uu, l, r, tprobes[__ffs(m) - 1], wabs, tb, n0 + s_begin + s);
         };
-        if constexpr (KH > 0 && SP && !US) {
+        if constexpr (EDGE_FAST && KH > 0 && SP && !US) {
+            // (resident tiles, where an edge or source tile paces every span)
             // free / refreshed warp windows of an edge or source tile: the warp's
             // choice (uniform across its lanes); a warp without special points
             // runs the bare (or recording) loop, one with them the edges-first
@@ -991,8 +992,8 @@ __global__ void __launch_bounds__(NT, MINB) span_kernel_res(const __grid_constan
         Real u[P], w[P];
         smem_to_regs<Real, P>(su + tb, u);
         smem_to_regs<Real, P>(sw + tb, w);
-        predict_tile<Real, FORM, P, NW, KH, 0, USRC>(prm, pr, td, u, w, gj0, n0, steps, tb, own_lo, own_hi, s_probes,
-                                                  np, xch, hx, warp, lane, edge);
+        predict_tile<Real, FORM, P, NW, KH, 0, USRC, true>(prm, pr, td, u, w, gj0, n0, steps, tb, own_lo, own_hi,
+                                                        s_probes, np, xch, hx, warp, lane, edge);
         __syncthreads();  // every window is read (KH > 0: they overlap) before owned points are written back
         owned_to_smem<Real, P, KH>(su + tb, u, own_lo, own_hi);
         owned_to_smem<Real, P, KH>(sw + tb, w, own_lo, own_hi);
