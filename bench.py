@@ -564,6 +564,23 @@ def profile_case(which: str, variant=None, span=None, full=False, log2_nx=22) ->
         b.check()
         print(json.dumps({"profile_case": which, "problems": len(probs), "T": probs[0].T, "info": b.info()}))
         return
+    if which == "g32":
+        # the c4 FP32 boundary gradient (the adjoint variables through the span
+        # kernel, source at j_r = 4000, probe at j = 1), 2^log2_nx points and
+        # 1024 steps, in the given variant; run twice
+        p = inputs.c4(T=1024, nx=1 << log2_nx, j_r=4000)
+        plan = rswr.Plan.from_problem(p, dtype=rswr.F32)
+        if variant is not None:
+            plan.set_span(span or 32)
+            plan.set_variant(variant)
+        fA = torch.as_tensor(p.fA, device="cuda").float()
+        w = torch.as_tensor(inputs.lowpass_noise(p.T, seed=4), device="cuda").float()
+        for _ in range(2):
+            plan.adjoint(fA, None, p.T, 4000, w, want_a=False)
+        torch.cuda.synchronize()
+        plan.check()
+        print(json.dumps({"profile_case": which, "nx": p.nx, "T": p.T, "info": plan.info()}))
+        return
     if which in ("adj64", "adj32"):
         # the c4 gradient workload (dL/dfA and dL/da), run twice; a smaller grid
         # (log2_nx < 20) scales the steps with it
@@ -978,7 +995,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mono", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched / adjoint / large-grid measurements")
-    ap.add_argument("--profile-case", choices=["f64", "f32", "adj64", "adj32", "c3"], default=None,
+    ap.add_argument("--profile-case", choices=["f64", "f32", "adj64", "adj32", "g32", "c3"], default=None,
                     help="run a small profiling case twice and exit (for ncu): f64/f32 nx=2^22, 1280 steps; "
                          "adj64/adj32 the c4 gradient; c3 the first 1024 batched problems, 256 steps")
     ap.add_argument("--variant", type=int, default=None, help="kernel variant of the profiling case")
@@ -997,7 +1014,7 @@ def main():
         NO_TRACES = args.no_traces
         lg = args.profile_log2_nx
         if lg is None:
-            lg = 20 if args.profile_case in ("adj64", "adj32") else 22
+            lg = 20 if args.profile_case in ("adj64", "adj32", "g32") else 22
         profile_case(args.profile_case, args.variant, args.span, args.full, lg)
         return
 
