@@ -206,7 +206,34 @@ __global__ void rswr_resolve_kernel(const __grid_constant__ PaperParams<Real> p)
     }
 }
 
+// The re-solved zones into the combined state: points [tile_lo, tile_hi) of
+// every zone tile, from the scratch pair (plain arrays) to the state pair.
+template <typename Real>
+__global__ void paper_scatter_kernel(const Real* su, const Real* sw, Real* du, Real* dw, const int64_t* lo,
+                                     const int64_t* hi)
+{
+    const int64_t t = blockIdx.x;
+    for (int64_t j = lo[t] + threadIdx.x; j < hi[t]; j += blockDim.x) {
+        du[j] = su[j];
+        dw[j] = sw[j];
+    }
+}
+
 }  // namespace
+
+cudaError_t paper_scatter_launch(int dtype, const void* su, const void* sw, void* du, void* dw, const int64_t* lo,
+                                 const int64_t* hi, int ntiles, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    if (dtype == kF64)
+        paper_scatter_kernel<double><<<ntiles, 128, 0, s>>>(static_cast<const double*>(su),
+                                                            static_cast<const double*>(sw), static_cast<double*>(du),
+                                                            static_cast<double*>(dw), lo, hi);
+    else
+        paper_scatter_kernel<float><<<ntiles, 128, 0, s>>>(static_cast<const float*>(su), static_cast<const float*>(sw),
+                                                           static_cast<float*>(du), static_cast<float*>(dw), lo, hi);
+    return cudaGetLastError();
+}
 
 cudaError_t paper_iface_launch(int dtype, const void* params, int n_iface, size_t smem, cudaStream_t s)
 {

@@ -121,6 +121,7 @@ struct Engine {
     // adjoint workspace (rswr_adjoint with dL/da): states, tables, partial sums
     void* adj_mem = nullptr;
     size_t adj_mem_cap = 0;
+    int* h_word = nullptr;  // pinned host word (the paper-literal span read back every span)
     // Span states of a forward run kept in adj_mem for the next rswr_adjoint
     // (rswr_run_keep): valid while `kept` holds and the key matches.
     struct KeptKey {
@@ -177,6 +178,7 @@ void free_engine(Engine* e)
     cudaFree(e->d_ticket);
     cudaFree(e->d_done);
     cudaFree(e->d_xbuf);
+    if (e->h_word) cudaFreeHost(e->h_word);
     cudaFree(e->d_err);
     cudaFree(e->d_host_stage);
     cudaFree(e->adj_mem);
@@ -442,6 +444,7 @@ struct RunReq {
     int64_t src_stride = 1;
     bool mono = false;
     bool user_src = false;  // apply the engine's user point sources
+    bool from_state = false;  // continue from the engine's state q[0] as it is (no level-0 set-up)
 };
 
 template <typename Real>
@@ -652,10 +655,12 @@ rswr_status device_work(Engine* e, const RunReq& r, int nprobe, int64_t mono_blk
 {
     const size_t es = sizeof(Real);
     rswr_status st = RSWR_OK;
-    RSWR_CUDA(cudaMemsetAsync(e->d_err, 0, sizeof(DevError), s));
+    if (!r.from_state) RSWR_CUDA(cudaMemsetAsync(e->d_err, 0, sizeof(DevError), s));
 
     // level-0 state into buffer 0
-    if (!r.q0) {
+    if (r.from_state) {
+        // the state is already in buffer 0 (a continued run)
+    } else if (!r.q0) {
         RSWR_CUDA(cudaMemsetAsync(e->q0[0], 0, es * e->state_len, s));
         RSWR_CUDA(cudaMemsetAsync(e->q1[0], 0, es * e->state_len, s));
     } else {
@@ -668,7 +673,8 @@ rswr_status device_work(Engine* e, const RunReq& r, int nprobe, int64_t mono_blk
             RSWR_CUDA(cudaMemsetAsync(e->q1[0], 0, es * e->state_len, s));
         }
     }
-    RSWR_CUDA(set_boundary_launch(e->dtype, e->form, e->q0[0], e->q1[0], e->d_problems, (int)e->probs.size(), s));
+    if (!r.from_state)
+        RSWR_CUDA(set_boundary_launch(e->dtype, e->form, e->q0[0], e->q1[0], e->d_problems, (int)e->probs.size(), s));
 
     const void* fin0;
     const void* fin1;
@@ -1565,6 +1571,17 @@ rswr_status autotune_engine(Engine* e, int64_t probe_steps, int32_t* variant, cu
 namespace {
 
 // ---- the paper-literal span loop (see paper_kernel.cu) --------------------
+// Per span: predict + select on every interface (rswr_iface_kernel, the span
+// read back to the host), then the update.  The update re-solves every
+// subdomain window over the span with the neighbours' predicted output fluxes
+// as Neumann data (Sec. 2.5).  A point farther than the span from both input
+// boundaries of its window depends only on the true state, through the same
+// operations as the monolithic leapfrog, so there the re-solve gives the
+// monolithic bits: the whole grid is advanced by the span kernel (the plan's
+// fast path, from the state it keeps), and only the kept points within the
+// span of an input boundary ("zones") are re-solved with the paper's rule
+// (rswr_resolve_kernel, from the span-start state into scratch, scattered into
+// the result).  Same bits as re-solving every window.
 template <typename Real>
 rswr_status run_paper(Engine* e, const Real* fA, const Real* fB, int64_t T, const Real* q0, const Real* q1, Real* out0,
                       Real* out1, int64_t* spans, int64_t spans_cap, int64_t* nspans, double beta, cudaStream_t s)
@@ -1581,23 +1598,31 @@ rswr_status run_paper(Engine* e, const Real* fA, const Real* fB, int64_t T, cons
     const int64_t tau_max = (std::max(tau, cap) * (1000 + beta_m) + 999) / 1000 + 1;
     auto wl = [&](int64_t i) { return std::max<int64_t>(i * nx / N - el, 0); };
     auto wr = [&](int64_t i) { return std::min<int64_t>((i + 1) * nx / N - 1 + er, nx - 1); };
-    // re-solve tiles: each subdomain's part of the combined solution, in chunks
+    // zone tiles: the kept points of subdomain i (from its left neighbour's
+    // window end on) within tau_max >= any span of an input boundary, in chunks
     constexpr int64_t CH = 1024;
     std::vector<int64_t> tsub, tlo, thi;
     for (int64_t i = 0; i < N; ++i) {
-        const int64_t from = (i == 0) ? wl(0) : wr(i - 1) + 1;
-        for (int64_t c = from; c <= wr(i); c += CH) {
-            tsub.push_back(i);
-            tlo.push_back(c);
-            thi.push_back(std::min(c + CH, wr(i) + 1));
-        }
+        const int64_t L = wl(i), R = wr(i);
+        const int64_t from = (i == 0) ? L : wr(i - 1) + 1;
+        std::vector<std::pair<int64_t, int64_t>> z;  // [lo, hi)
+        if (i > 0 && L > 0 && L + tau_max - 1 >= from) z.push_back({from, std::min(R, L + tau_max - 1) + 1});
+        if (i + 1 < N && R < nx - 1) z.push_back({std::max(from, R - tau_max + 1), R + 1});
+        if (z.size() == 2 && z[1].first <= z[0].second) z = {{z[0].first, z[1].second}};
+        for (auto& r : z)
+            for (int64_t c = r.first; c < r.second; c += CH) {
+                tsub.push_back(i);
+                tlo.push_back(c);
+                thi.push_back(std::min(c + CH, r.second));
+            }
     }
     const int64_t nt = (int64_t)tsub.size();
-    // workspace: two plain state pairs, flux waveforms, tiles, span word
+    // workspace: the zones' scratch pair, flux waveforms, tiles, span word
     auto up = [](size_t x) { return (x + 255) / 256 * 256; };
     const size_t b_state = up(es * nx);
     const size_t b_g = up(es * N * tau_max);
-    const size_t need = 4 * b_state + 2 * b_g + 3 * up(sizeof(int64_t) * nt) + 256;
+    const size_t b_t = up(sizeof(int64_t) * std::max<int64_t>(nt, 1));
+    const size_t need = 2 * b_state + 2 * b_g + 3 * b_t + 256;
     if (need > e->adj_mem_cap) {
         RSWR_CUDA(cudaStreamSynchronize(s));
         cudaFree(e->adj_mem);
@@ -1607,35 +1632,40 @@ rswr_status run_paper(Engine* e, const Real* fA, const Real* fB, int64_t T, cons
         e->adj_mem_cap = need;
     }
     char* m = static_cast<char*>(e->adj_mem);
-    Real* X0 = reinterpret_cast<Real*>(m);
-    Real* X1 = reinterpret_cast<Real*>(m + b_state);
-    Real* Y0 = reinterpret_cast<Real*>(m + 2 * b_state);
-    Real* Y1 = reinterpret_cast<Real*>(m + 3 * b_state);
-    Real* gL = reinterpret_cast<Real*>(m + 4 * b_state);
-    Real* gR = reinterpret_cast<Real*>(m + 4 * b_state + b_g);
-    int64_t* d_sub = reinterpret_cast<int64_t*>(m + 4 * b_state + 2 * b_g);
-    int64_t* d_lo = d_sub + up(sizeof(int64_t) * nt) / sizeof(int64_t);
-    int64_t* d_hi = d_lo + up(sizeof(int64_t) * nt) / sizeof(int64_t);
-    int* d_span = reinterpret_cast<int*>(d_hi + up(sizeof(int64_t) * nt) / sizeof(int64_t));
-    RSWR_CUDA(cudaMemcpyAsync(d_sub, tsub.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice, s));
-    RSWR_CUDA(cudaMemcpyAsync(d_lo, tlo.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice, s));
-    RSWR_CUDA(cudaMemcpyAsync(d_hi, thi.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice, s));
+    Real* Y0 = reinterpret_cast<Real*>(m);
+    Real* Y1 = reinterpret_cast<Real*>(m + b_state);
+    Real* gL = reinterpret_cast<Real*>(m + 2 * b_state);
+    Real* gR = reinterpret_cast<Real*>(m + 2 * b_state + b_g);
+    int64_t* d_sub = reinterpret_cast<int64_t*>(m + 2 * b_state + 2 * b_g);
+    int64_t* d_lo = reinterpret_cast<int64_t*>(m + 2 * b_state + 2 * b_g + b_t);
+    int64_t* d_hi = reinterpret_cast<int64_t*>(m + 2 * b_state + 2 * b_g + 2 * b_t);
+    int* d_span = reinterpret_cast<int*>(m + 2 * b_state + 2 * b_g + 3 * b_t);
+    if (nt > 0) {
+        RSWR_CUDA(cudaMemcpyAsync(d_sub, tsub.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice, s));
+        RSWR_CUDA(cudaMemcpyAsync(d_lo, tlo.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice, s));
+        RSWR_CUDA(cudaMemcpyAsync(d_hi, thi.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice, s));
+    }
 
-    // level 0 (paper Sec. 2.1, or the given state), boundary nodes from the samples
-    if (q0) RSWR_CUDA(cudaMemcpyAsync(X0, q0, es * nx, cudaMemcpyDeviceToDevice, s));
-    else RSWR_CUDA(cudaMemsetAsync(X0, 0, es * nx, s));
-    if (q1) RSWR_CUDA(cudaMemcpyAsync(X1, q1, es * nx, cudaMemcpyDeviceToDevice, s));
-    else if (q0 && e->form == kCanonical) RSWR_CUDA(cudaMemcpyAsync(X1, q0, es * nx, cudaMemcpyDeviceToDevice, s));
-    else RSWR_CUDA(cudaMemsetAsync(X1, 0, es * nx, s));
-    ProblemDev<Real> pb{};
-    pb.base = 0;
-    pb.nx = nx;
-    pb.fA = fA;
-    pb.fB = fB;
-    ProblemDev<Real>* d_pb = reinterpret_cast<ProblemDev<Real>*>(e->d_problems);
-    RSWR_CUDA(cudaMemcpyAsync(d_pb, &pb, sizeof(pb), cudaMemcpyHostToDevice, s));
-    RSWR_CUDA(set_boundary_launch(e->dtype, e->form, X0, X1, d_pb, 1, s));
-    RSWR_CUDA(cudaStreamSynchronize(s));  // pb is on the stack
+    // level 0 (paper Sec. 2.1, or the given state) in the plan's own state
+    // arrays; the runs below continue from there (no graph capture: the span
+    // kernel's arguments change every span)
+    const bool keep_graph = e->use_graph;
+    e->use_graph = false;
+    struct Restore {
+        Engine* e;
+        bool g;
+        ~Restore() { e->use_graph = g; }
+    } restore{e, keep_graph};
+    {
+        RunReq r;
+        r.fA = fA;
+        r.fB = fB;
+        r.T = 0;
+        r.q0 = q0;
+        r.q1 = q1;
+        rswr_status st = run_impl<Real>(e, r, s);
+        if (st != RSWR_OK) return st;
+    }
 
     PaperParams<Real> pp{};
     pp.fA = fA;
@@ -1656,39 +1686,63 @@ rswr_status run_paper(Engine* e, const Real* fA, const Real* fB, int64_t T, cons
     pp.k = sizeof(Real) == 8 ? (Real)ph.k : (Real)ph.kf;
     const double dx = (ph.xb - ph.xa) / (double)(nx - 1);
     pp.two_dx = (Real)(2.0 * dx);
+    if (!e->h_word && cudaMallocHost(&e->h_word, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        e->h_word = nullptr;
+        return fail(RSWR_ENOMEM, "pinned host word");
+    }
     int64_t m_count = 0;
     for (int64_t n0 = 0; n0 < T;) {
+        // the state at level n0, indexed by grid point
+        Real* cu = static_cast<Real*>(e->q0[0]) + ph.base;
+        Real* cw = static_cast<Real*>(e->q1[0]) + ph.base;
         const int steps = (int)std::min<int64_t>(tau, T - n0);
-        pp.u = X0;
-        pp.w = X1;
+        pp.u = cu;
+        pp.w = cw;
         pp.n0 = n0;
         pp.steps = steps;
-        RSWR_CUDA(cudaMemcpyAsync(d_span, &steps, sizeof(int), cudaMemcpyHostToDevice, s));
+        // predict + select (Sec. 2.3, 2.4, Sec. 3): every pair lowers the span
+        // word (bytes 0x7f: a value above any span) with atomicMin
+        RSWR_CUDA(cudaMemsetAsync(d_span, 0x7f, sizeof(int), s));
         const size_t smem_i = es * (8 * (size_t)(ov + steps + 2)) + sizeof(int) * (size_t)(ov + 2);
         RSWR_CUDA(paper_iface_launch(e->dtype, &pp, (int)(N - 1), smem_i, s));
-        int span = steps;
-        RSWR_CUDA(cudaMemcpyAsync(&span, d_span, sizeof(int), cudaMemcpyDeviceToHost, s));
+        RSWR_CUDA(cudaMemcpyAsync(e->h_word, d_span, sizeof(int), cudaMemcpyDeviceToHost, s));
         RSWR_CUDA(cudaStreamSynchronize(s));
+        int span = std::min(*e->h_word, steps);
         if (span > cap) span = (int)cap;
         if (span < 1) span = 1;
+        // update (Sec. 2.5): the zones next to input boundaries from the span-start state
         pp.steps = span;
         pp.uo = Y0;
         pp.wo = Y1;
-        const size_t smem_r = es * 4 * (size_t)(CH + 2 * span + 2);
-        RSWR_CUDA(paper_resolve_launch(e->dtype, &pp, (int)nt, smem_r, s));
+        if (nt > 0) {
+            const size_t smem_r = es * 4 * (size_t)(CH + 2 * span + 2);
+            RSWR_CUDA(paper_resolve_launch(e->dtype, &pp, (int)nt, smem_r, s));
+        }
+        // ... and every other point through the span kernel
+        RunReq r;
+        r.fA = fA ? fA + n0 : nullptr;
+        r.fB = fB ? fB + n0 : nullptr;
+        r.T = span;
+        r.from_state = true;
+        rswr_status st = run_impl<Real>(e, r, s);
+        if (st != RSWR_OK) return st;
+        if (((span + e->S - 1) / e->S) & 1) {  // the result is in buffer 1: make it the current state
+            std::swap(e->q0[0], e->q0[1]);
+            std::swap(e->q1[0], e->q1[1]);
+        }
+        RSWR_CUDA(paper_scatter_launch(e->dtype, Y0, Y1, static_cast<Real*>(e->q0[0]) + ph.base,
+                                       static_cast<Real*>(e->q1[0]) + ph.base, d_lo, d_hi, (int)nt, s));
         if (spans && m_count < spans_cap) spans[m_count] = span;
         ++m_count;
         n0 += span;
-        std::swap(X0, Y0);
-        std::swap(X1, Y1);
         tau = ((int64_t)span * (1000 + beta_m) + 999) / 1000;
         if (tau > tau_max) tau = tau_max;
     }
     if (nspans) *nspans = m_count;
-    RSWR_CUDA(cudaMemcpyAsync(out0, X0, es * nx, cudaMemcpyDeviceToDevice, s));
-    RSWR_CUDA(cudaMemcpyAsync(out1, X1, es * nx, cudaMemcpyDeviceToDevice, s));
-    RSWR_CUDA(cudaStreamSynchronize(s));
-    return RSWR_OK;
+    RSWR_CUDA(cudaMemcpyAsync(out0, static_cast<Real*>(e->q0[0]) + ph.base, es * nx, cudaMemcpyDeviceToDevice, s));
+    RSWR_CUDA(cudaMemcpyAsync(out1, static_cast<Real*>(e->q1[0]) + ph.base, es * nx, cudaMemcpyDeviceToDevice, s));
+    return check_engine(e, s, nullptr, nullptr, nullptr);
 }
 
 }  // namespace

@@ -215,6 +215,8 @@ cudaError_t adj_reduce_launch(const double* partial, int64_t nspans, int64_t nti
                               cudaStream_t s);
 
 // paper_kernel.cu
+cudaError_t paper_scatter_launch(int dtype, const void* su, const void* sw, void* du, void* dw, const int64_t* lo,
+                                 const int64_t* hi, int ntiles, cudaStream_t s);
 cudaError_t paper_iface_launch(int dtype, const void* params, int n_iface, size_t smem, cudaStream_t s);
 cudaError_t paper_resolve_launch(int dtype, const void* params, int ntiles, size_t smem, cudaStream_t s);
 
