@@ -825,6 +825,7 @@ def bench_paper_literal(torch, dev, T=2000):
     res = {"workload": "c2 grid, 2000 steps, paper-literal select/update", "unit": UNIT}
     for name, dtype in (("f64", rswr.F64), ("f32", rswr.F32)):
         plan = rswr.Plan.from_problem(p, dtype=dtype, device=dev)
+        plan.autotune(64)  # the span kernel that advances the grid each span
         td = torch.float64 if dtype == rswr.F64 else torch.float32
         fA = torch.as_tensor(p.fA, device=dev).to(td)
         out = (torch.empty(p.nx, dtype=td, device=dev), torch.empty(p.nx, dtype=td, device=dev))
