@@ -20,11 +20,18 @@
 // leapfrog step, source) -> TMA store of lambda's core -> one double per tile
 // (block reduction in a fixed order; the host sums tiles and spans in a fixed
 // order too, so the result is deterministic).
+//
+// The FP32 persistent sweep keeps the Laplacians in tensor memory instead
+// (TMEM, tmem.cuh): a thread's P values of level s in columns [s P, s P + P) of
+// its own lane.  Shared memory then holds only the staged windows, so twice as
+// many CTAs fit on an SM; the values and the order of every operation are the
+// same, so the results are bit-identical to the shared-memory store.
 
 #include <algorithm>
 
 #include "rswr_internal.h"
 #include "span_common.cuh"
+#include "tmem.cuh"
 
 namespace rswr {
 
@@ -51,11 +58,14 @@ struct AdjTile {
 // The adjoint pair is written back to stage[2..3].  Returns this thread's part of
 // sum lambda^{n+1} lap(u^n).  BAR: the barrier of the window's threads; `buf`
 // (the exchange-slot parity) continues across calls so that consecutive
-// exchanges always alternate slots.
-template <typename Real, int FORM, int P, int NT, int SA, int BAR>
+// exchanges always alternate slots.  TM: the Laplacians go to tensor memory at
+// tm (this warp's first lane, column 0) instead of `laps`.
+template <typename Real, int FORM, int P, int NT, int SA, int BAR, bool TM = false>
 __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTile<Real>& at, Real* stage, Real* laps,
-                                         Real* xch, int& buf)
+                                         Real* xch, int& buf, uint32_t tm = 0)
 {
+    static_assert(!TM || (sizeof(Real) == 4 && P % 8 == 0 && NT == 128),
+                  "TMEM store: FP32 words, whole 8-column chunks, one warp per lane quadrant");
     constexpr int W = NT * P;
     constexpr int NW = NT / 32;
     const int tid = threadIdx.x;
@@ -109,7 +119,12 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
             Real lft, rgt;
             exchange<Real, P, NW, BAR>(u, lft, rgt, xch, buf, warp, lane);
             buf ^= 1;
-            Real* lp = laps + s * W + lap_base;  // point i of this thread at lp[i * lap_stride]
+            [[maybe_unused]] Real* lp = laps + s * W + lap_base;  // point i of this thread at lp[i * lap_stride]
+            [[maybe_unused]] Real lv[P];  // TM: the level's Laplacians, stored after the pass
+            auto put = [&](int i, Real x) {
+                if constexpr (TM) lv[i] = x;
+                else lp[i * lap_stride] = x;
+            };
             // one pass: the Laplacian of this level (from the step's own neighbour
             // sum, (uL + uR) - 2u = fma(-2, u, uL + uR) exactly) and the step
             if constexpr (FORM == kCanonical) {
@@ -119,7 +134,7 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
                     const Real uc = u[i];
                     const Real ur = i < P - 1 ? u[i + 1] : rgt;
                     const Real sum = radd(ul, ur);
-                    lp[i * lap_stride] = rfma(Real(-2), uc, sum);
+                    put(i, rfma(Real(-2), uc, sum));
                     if constexpr (STEP) {
                         u[i] = rfma(c2, sum, rfma(kk, uc, -w[i]));
                         w[i] = uc;
@@ -134,12 +149,21 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
                     const Real d = rsub(ur, u[i]);
                     const Real lap = rsub(d, d_prev);
                     d_prev = d;
-                    lp[i * lap_stride] = lap;
+                    put(i, lap);
                     if constexpr (STEP) {
                         const Real v = rfma(c2, lap, w[i]);
                         w[i] = v;
                         u[i] = radd(u[i], v);
                     }
+                }
+            }
+            if constexpr (TM) {
+#pragma unroll
+                for (int c = 0; c < P / 8; ++c) {
+                    uint32_t b[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) b[q] = __float_as_uint(lv[8 * c + q]);
+                    tmem_st8(tm + (uint32_t)(s * P + 8 * c), b);
                 }
             }
             if constexpr (STEP) {
@@ -167,6 +191,7 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
         };
         for (int s = 0; s + 1 < len; ++s) level(std::true_type{}, s);
         if (len > 0) level(std::false_type{}, len - 1);
+        if constexpr (TM) tmem_wait_st();  // the lambda phase loads what this thread stored
     }
 
     // ---- lambda phase: levels m0 .. m0+len-1 pair with u levels n0+len-1 .. n0
@@ -195,6 +220,14 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
     const int ilo = (int)(jlo - gj <= 0 ? 0 : (jlo - gj >= P ? P : jlo - gj));
     const int ihi = (int)(jhi - gj <= 0 ? 0 : (jhi - gj >= P ? P : jhi - gj));
     for (int s = 0; s < len; ++s) {
+        // TM: the pairing level's Laplacians are fetched while the neighbours
+        // are exchanged
+        uint32_t lb[TM ? P : 1];
+        if constexpr (TM) {
+#pragma unroll
+            for (int c = 0; c < P / 8; ++c)
+                tmem_ld8(tm + (uint32_t)((len - 1 - s) * P + 8 * c), *reinterpret_cast<uint32_t(*)[8]>(lb + 8 * c));
+        }
         Real lft, rgt;
         exchange<Real, P, NW, BAR>(l, lft, rgt, xch, buf, warp, lane);
         buf ^= 1;
@@ -203,10 +236,19 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
             record_probes<Real, P>(l, lft, rgt, wabs, tid * P, 0, P, at.td.probe_begin, at.td.probe_end, prm.probes,
                                    m);
         // each thread reads the Laplacians of its own points only
-        const Real* lp = laps + (len - 1 - s) * W + lap_base;
+        if constexpr (TM) {
+            __syncwarp();
 #pragma unroll
-        for (int i = 0; i < P; ++i)
-            if (i >= ilo && i < ihi) racc = rfma(l[i], lp[i * lap_stride], racc);
+            for (int c = 0; c < P / 8; ++c) tmem_wait_ld(*reinterpret_cast<uint32_t(*)[8]>(lb + 8 * c));
+#pragma unroll
+            for (int i = 0; i < P; ++i)
+                if (i >= ilo && i < ihi) racc = rfma(l[i], __uint_as_float(lb[i]), racc);
+        } else {
+            const Real* lp = laps + (len - 1 - s) * W + lap_base;
+#pragma unroll
+            for (int i = 0; i < P; ++i)
+                if (i >= ilo && i < ihi) racc = rfma(l[i], lp[i * lap_stride], racc);
+        }
         Real sval = Real(0);  // src at level m + 1
         if (wsrc) {
             if (s - sbase == 32) {
@@ -499,23 +541,43 @@ __device__ void adj_producer(const AdjParams<Real>& prm, Real* stage, uint64_t* 
         if ((armed >> st) & 1u) mbar_wait_bounded(&full_bar[st], ((fpar >> st) & 1u) ^ 1u, prm.wait_ns, nullptr);
 }
 
-template <typename Real, int FORM, int P, int NT, int SA>
+// Columns of tensor memory a CTA of the TMEM variant allocates: SA levels of P
+// words per lane, rounded up to a power of two (at least 32).
+__host__ __device__ constexpr int tmem_cols(int n)
+{
+    int c = 32;
+    while (c < n) c *= 2;
+    return c;
+}
+
+template <typename Real, int FORM, int P, int NT, int SA, bool TM>
 __global__ void __launch_bounds__(NT + 32) adjoint_kernel_ws(const __grid_constant__ AdjParams<Real> prm)
 {
     constexpr int W = NT * P;
     constexpr int NW = NT / 32;
+    constexpr uint32_t NCOL = (uint32_t)tmem_cols(SA * P);
+    static_assert(!TM || NCOL <= 512, "the Laplacian store exceeds the tensor memory of an SM");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Real* stage = reinterpret_cast<Real*>(smem_raw);  // [2 stages][4][W]
-    Real* laps = stage + 8 * W;                       // [SA][W]
-    Real* xch = laps + SA * W;                        // [2][NW][2]
+    Real* laps = stage + 8 * W;                       // [SA][W] (not with TM)
+    Real* xch = laps + (TM ? 0 : SA * W);             // [2][NW][2]
     __shared__ __align__(8) uint64_t full_bar[2];
     __shared__ __align__(8) uint64_t empty_bar[2];
     __shared__ __align__(16) AdjStage<Real> s_info[2];
     __shared__ double red[NW];
+    __shared__ uint32_t s_tmem;
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
+    if constexpr (TM) {
+        // before the producer takes a ticket: a CTA that waited here would hold none
+        if (warp == 0) {
+            tmem_alloc(&s_tmem, NCOL);
+            tmem_relinquish();
+        }
+        tmem_fence_before_sync();
+    }
     if (tid == NT) {
         mbar_init(&full_bar[0], 1);
         mbar_init(&full_bar[1], 1);
@@ -528,6 +590,11 @@ __global__ void __launch_bounds__(NT + 32) adjoint_kernel_ws(const __grid_consta
     if (warp == NW) {
         if (lane == 0) adj_producer<Real, W>(prm, stage, full_bar, empty_bar, s_info);
         return;
+    }
+    uint32_t tm = 0;
+    if constexpr (TM) {
+        tmem_fence_after_sync();
+        tm = tmem_addr(s_tmem, 32u * (uint32_t)(warp & 3), 0u);
     }
     uint32_t fpar = 0u;
     int y = 0, buf = 0;
@@ -547,13 +614,23 @@ __global__ void __launch_bounds__(NT + 32) adjoint_kernel_ws(const __grid_consta
         at.m0 = si.m0;
         at.len = si.len;
         Real* st = stage + y * 4 * W;
-        const Real racc = adj_tile<Real, FORM, P, NT, SA, NT>(prm, at, st, laps, xch, buf);
+        const Real racc = adj_tile<Real, FORM, P, NT, SA, NT, TM>(prm, at, st, laps, xch, buf, tm);
         const double t = block_sum<NT, NT>((double)racc, red);
         if (tid == 0) prm.partial[(int64_t)(prm.nspans - 1 - si.kp) * prm.ntiles + si.tile] = t;
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty_bar[y]);
         y ^= 1;
+    }
+    if constexpr (TM) {
+        // every compute thread leaves the loop together (both exits are decided
+        // for all of them), with no TMEM access in flight
+        tmem_fence_before_sync();
+        block_sync<NT>();
+        if (warp == 0) {
+            tmem_fence_after_sync();
+            tmem_dealloc(s_tmem, NCOL);
+        }
     }
 }
 
@@ -689,29 +766,93 @@ namespace {
 struct WsEntry {
     int dtype, form, W, SA, threads;
     const void* fn;
-    size_t smem;
+    size_t smem;      // dynamic shared memory the kernel uses
+    int tmem_cols;    // TMEM columns per CTA (0: Laplacians in shared memory)
 };
 
-template <typename Real, int FORM, int P, int NT, int SA>
+template <typename Real, int FORM, int P, int NT, int SA, bool TM>
 WsEntry make_ws()
 {
     constexpr int W = NT * P;
     return WsEntry{sizeof(Real) == 8 ? kF64 : kF32, FORM, W, SA, NT + 32,
-                   reinterpret_cast<const void*>(&adjoint_kernel_ws<Real, FORM, P, NT, SA>),
-                   sizeof(Real) * ((8 + SA) * W + 4 * (NT / 32))};
+                   reinterpret_cast<const void*>(&adjoint_kernel_ws<Real, FORM, P, NT, SA, TM>),
+                   sizeof(Real) * ((8 + (TM ? 0 : SA)) * W + 4 * (NT / 32)), TM ? tmem_cols(SA * P) : 0};
 }
 
 const WsEntry* ws_find(int dtype, int form)
 {
     static const WsEntry entries[] = {
-        make_ws<double, kCanonical, 4, 128, 8>(),
-        make_ws<double, kIncrement, 4, 128, 8>(),
-        make_ws<float, kIncrement, 8, 128, 16>(),
-        make_ws<float, kCanonical, 8, 128, 16>(),
+        make_ws<double, kCanonical, 4, 128, 8, false>(),
+        make_ws<double, kIncrement, 4, 128, 8, false>(),
+        make_ws<float, kIncrement, 8, 128, 16, true>(),
+        make_ws<float, kCanonical, 8, 128, 16, true>(),
     };
     for (const WsEntry& e : entries)
         if (e.dtype == dtype && e.form == form) return &e;
     return nullptr;
+}
+
+// CTAs of the kernel that fit on one SM with `smem` bytes of dynamic shared
+// memory, from its shared memory, registers and threads.  The runtime's
+// occupancy calculator answers 1 for any kernel that allocates tensor memory
+// (it cannot know how many columns a CTA takes), while the SM holds as many
+// such CTAs as these three resources allow; 0 if an attribute is unavailable.
+int resident_ctas(const void* fn, int threads, size_t smem)
+{
+    int dev = 0, per_sm = 0, regs_sm = 0, thr_sm = 0, blk_sm = 0;
+    cudaFuncAttributes fa{};
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int warps = (threads + 31) / 32;
+    // shared memory: dynamic + static + the 1 KiB the runtime reserves per CTA
+    const long long per_cta = (long long)smem + (long long)fa.sharedSizeBytes + 1024;
+    // registers: allocated per warp in units of 256
+    const long long regs_warp = ((long long)fa.numRegs * 32 + 255) / 256 * 256;
+    long long n = per_sm / per_cta;
+    if (regs_warp > 0) n = std::min<long long>(n, regs_sm / (regs_warp * warps));
+    n = std::min<long long>(n, thr_sm / (warps * 32));
+    n = std::min<long long>(n, blk_sm);
+    return (int)std::max<long long>(n, 0);
+}
+
+// Dynamic shared memory of a launch.  With a TMEM store the CTAs of one SM
+// must not ask for more than its 512 columns together, so the launch asks for
+// enough shared memory that no more than 512 / tmem_cols CTAs fit; 0 if that
+// cannot be arranged.
+size_t ws_launch_smem(const WsEntry& e)
+{
+    if (e.tmem_cols == 0) return e.smem;
+    int dev = 0, per_sm = 0, per_block = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, e.fn) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int cap = 512 / e.tmem_cols;
+    // cap CTAs of (dynamic + static + the 1 KiB the runtime reserves) fill the SM
+    long long want = (long long)per_sm / cap - (long long)fa.sharedSizeBytes - 1024;
+    if (want + (long long)fa.sharedSizeBytes > per_block) want = per_block - (long long)fa.sharedSizeBytes;
+    want = want / 1024 * 1024;
+    if (want < (long long)e.smem) return 0;
+    if (cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int bps = resident_ctas(e.fn, e.threads, (size_t)want);
+    return (bps >= 1 && bps <= cap) ? (size_t)want : 0;
 }
 
 }  // namespace
@@ -732,7 +873,9 @@ cudaError_t adj_ws_prepare(int dtype, int form)
 {
     const WsEntry* e = ws_find(dtype, form);
     if (!e) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(e->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem);
+    const size_t smem = ws_launch_smem(*e);
+    if (smem == 0) return cudaErrorInvalidConfiguration;
+    return cudaFuncSetAttribute(e->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 cudaError_t adj_ws_occupancy(int dtype, int form, int* blocks_per_sm)
@@ -741,15 +884,21 @@ cudaError_t adj_ws_occupancy(int dtype, int form, int* blocks_per_sm)
     if (!e) return cudaErrorInvalidValue;
     cudaError_t st = adj_ws_prepare(dtype, form);
     if (st != cudaSuccess) return st;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, e->fn, e->threads, e->smem);
+    if (e->tmem_cols > 0) {
+        *blocks_per_sm = resident_ctas(e->fn, e->threads, ws_launch_smem(*e));
+        return cudaSuccess;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, e->fn, e->threads, ws_launch_smem(*e));
 }
 
 cudaError_t adj_ws_launch(int dtype, int form, const void* params, int grid, cudaStream_t s)
 {
     const WsEntry* e = ws_find(dtype, form);
     if (!e) return cudaErrorInvalidValue;
+    const size_t smem = ws_launch_smem(*e);
+    if (smem == 0) return cudaErrorInvalidConfiguration;
     void* args[] = {const_cast<void*>(params)};
-    return cudaLaunchKernel(e->fn, dim3(grid), dim3(e->threads), args, e->smem, s);
+    return cudaLaunchKernel(e->fn, dim3(grid), dim3(e->threads), args, smem, s);
 }
 
 cudaError_t adj_init_launch(int dtype, int form, void* l0, void* l1, const void* prob_l, int nprob, const void* wbar,

@@ -462,6 +462,32 @@ def test_adjoint_grad_a_fp32(R, oracle_mod, spacing):
     assert np.linalg.norm(got - ref["dg"]) <= 1e-4 * np.linalg.norm(ref["dg"])
 
 
+def test_persistent_adjoint_equals_per_span_adjoint_bitwise(R):
+    """FP32: the persistent adjoint sweep (every span state kept, the
+    Laplacians in tensor memory) and the per-span launches of the checkpointed
+    path (Laplacians in shared memory) use the same tiles and do the same
+    operations in the same order, so their gradients agree bit for bit.
+    250 spans of 16 steps (the last one ragged), 8 tiles per span.  (In FP64
+    the two kernels tile the grid differently, so dL/da is summed in another
+    order there.)"""
+    dtype = F32
+    nx, N, ov, T, jr = 8001, 8, 64, 4001, 2500
+    a = 1.3
+    dt = 0.9 / (nx - 1) / a
+    g = inputs.lowpass_noise(T, seed=4)
+    w = inputs.rng(9).standard_normal(T + 1)
+    out = []
+    for spacing in (0, 6):
+        plan = R.Plan(0.0, 1.0, a, nx, dt, N, ov, dtype=dtype)
+        plan.set_checkpoint_spacing(spacing)
+        res = plan.adjoint(g, None, T, jr, w, want_a=True)
+        plan.check()
+        out.append((host(res["grad_fA"]), res["grad_a"].item()))
+    assert np.abs(out[0][0]).max() > 0 and out[0][1] != 0.0
+    assert_bitwise(out[0][0], out[1][0], "grad_fA, persistent vs per-span")
+    assert out[0][1] == out[1][1], (out[0][1], out[1][1])
+
+
 @pytest.mark.parametrize("spacing", [0, 5])
 def test_batch_adjoint_with_grad_a(R, oracle_mod, spacing):
     r = inputs.rng(17)
