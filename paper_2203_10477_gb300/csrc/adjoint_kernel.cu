@@ -272,6 +272,198 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
     return racc;
 }
 
+// The same tile with free warp windows (FP32, Laplacians in TMEM).  Warp w
+// works on the 32 P points of the tile window from w (32 P - 2 KH) on and owns
+// the middle 32 P - 2 KH of them; its neighbours come from shuffles only, with
+// mirror ghosts at the ends of its window, so no level waits for the other
+// warps.  A level loses one valid point at each end of a warp window, and
+// KH >= len keeps the owned points exact (the Waveform Time Span argument on
+// the warp window).  The owned points of the four warps are the tile core
+// [KH, W - KH), so the tile halo is KH.  The adjoint pair goes to `out`
+// ([2][W]), not back to the stage: a neighbouring warp may still have to read
+// its halo from the stage.  Every point update and every pairing is the same
+// operation on the same operands as in adj_tile, so the bits are the same.
+template <typename Real, int FORM, int P, int NT, int SA, int KH>
+__device__ __forceinline__ Real adj_tile_fw(const AdjParams<Real>& prm, const AdjTile<Real>& at, const Real* stage,
+                                            Real* out, uint32_t tm)
+{
+    constexpr int NW = NT / 32;
+    constexpr int WO = 32 * P - 2 * KH;  // points a warp owns
+    constexpr int W = NW * WO + 2 * KH;  // tile window
+    static_assert(sizeof(Real) == 4 && P % 8 == 0 && NT == 128, "TMEM store: FP32, 8-column chunks, 4 warps");
+    static_assert(KH % P == 0 && KH >= SA && WO > 0, "warp halo: whole threads, at least one span long");
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int tb = warp * WO + lane * P;  // the thread's first point in the tile window
+    const bool own = lane >= KH / P && lane < 32 - KH / P;
+    const ProblemDev<Real>& pu = *at.pu;
+    const ProblemDev<Real>& pl = *at.pl;
+    const int64_t nx = pu.nx;
+    const int64_t gj0 = at.gj0;
+    const int64_t wabs = pu.base + gj0;
+    const int64_t gj = gj0 + tb;
+    const Real c2 = pu.c2, kk = pu.k;
+    const bool edge = (gj0 <= 0) || (gj0 + W - 1 >= nx - 1);
+    const bool has_src = pl.js >= 0 && pl.js >= gj0 && pl.js < gj0 + W;
+    const int len = at.len;
+
+    // ---- u phase: levels n0 .. n0+len-1, their Laplacians to TMEM
+    {
+        Real u[P], w[P];
+        smem_to_regs<Real, P>(stage + 0 * W + tb, u);
+        smem_to_regs<Real, P>(stage + 1 * W + tb, w);
+        const Special sp = make_special<P>(gj, nx, -1);
+        const bool special = edge && any_special(sp);
+        WarpChunk<Real> ca{}, cb{};
+        bool wa = false, wb = false;
+        int cbase = 0;
+        if (edge) {
+            wa = __any_sync(kFull, sp.r0 >= 0) && pu.fA != nullptr;
+            wb = __any_sync(kFull, sp.r1 >= 0) && pu.fB != nullptr;
+            if (wa) {
+                ca.c0 = level_sample(pu.fA, 1, at.n0 + lane, prm.T);
+                ca.c1 = level_sample(pu.fA, 1, at.n0 + 32 + lane, prm.T);
+            }
+            if (wb) {
+                cb.c0 = level_sample(pu.fB, 1, at.n0 + lane, prm.T);
+                cb.c1 = level_sample(pu.fB, 1, at.n0 + 32 + lane, prm.T);
+            }
+        }
+        auto level = [&](auto step_c, int s) {
+            constexpr bool STEP = decltype(step_c)::value;
+            Real lft, rgt;
+            warp_neighbours<Real, P>(u, lft, rgt, lane);
+            uint32_t b[P];
+            if constexpr (FORM == kCanonical) {
+                Real ul = lft;
+#pragma unroll
+                for (int i = 0; i < P; ++i) {
+                    const Real uc = u[i];
+                    const Real ur = i < P - 1 ? u[i + 1] : rgt;
+                    const Real sum = radd(ul, ur);
+                    b[i] = __float_as_uint(rfma(Real(-2), uc, sum));
+                    if constexpr (STEP) {
+                        u[i] = rfma(c2, sum, rfma(kk, uc, -w[i]));
+                        w[i] = uc;
+                    }
+                    ul = uc;
+                }
+            } else {
+                Real d_prev = rsub(u[0], lft);
+#pragma unroll
+                for (int i = 0; i < P; ++i) {
+                    const Real ur = i < P - 1 ? u[i + 1] : rgt;
+                    const Real d = rsub(ur, u[i]);
+                    const Real lap = rsub(d, d_prev);
+                    d_prev = d;
+                    b[i] = __float_as_uint(lap);
+                    if constexpr (STEP) {
+                        const Real v = rfma(c2, lap, w[i]);
+                        w[i] = v;
+                        u[i] = radd(u[i], v);
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < P / 8; ++c)
+                tmem_st8(tm + (uint32_t)(s * P + 8 * c), *reinterpret_cast<const uint32_t(*)[8]>(b + 8 * c));
+            if constexpr (STEP) {
+                if (s - cbase == 32) {
+                    cbase += 32;
+                    ca.c0 = ca.c1;
+                    cb.c0 = cb.c1;
+                    if (wa) ca.c1 = level_sample(pu.fA, 1, at.n0 + cbase + 32 + lane, prm.T);
+                    if (wb) cb.c1 = level_sample(pu.fB, 1, at.n0 + cbase + 32 + lane, prm.T);
+                }
+                Real fa_old = Real(0), fa_new = Real(0), fb_old = Real(0), fb_new = Real(0);
+                if (wa) {
+                    fa_old = ca.get(s - cbase);
+                    fa_new = ca.get(s - cbase + 1);
+                }
+                if (wb) {
+                    fb_old = cb.get(s - cbase);
+                    fb_new = cb.get(s - cbase + 1);
+                }
+                if (special)
+                    patch_special<Real, FORM, P>(u, w, sp, Real(0), Real(0), fa_old, fa_new, fb_old, fb_new);
+            }
+        };
+        for (int s = 0; s + 1 < len; ++s) level(std::true_type{}, s);
+        if (len > 0) level(std::false_type{}, len - 1);
+        tmem_wait_st();  // the lambda phase loads what this thread stored
+    }
+
+    // ---- lambda phase: levels m0 .. m0+len-1 pair with u levels n0+len-1 .. n0
+    Real racc = Real(0);
+    Real l[P], lw[P];
+    smem_to_regs<Real, P>(stage + 2 * W + tb, l);
+    smem_to_regs<Real, P>(stage + 3 * W + tb, lw);
+    const Special sp = make_special<P>(gj, nx, has_src ? pl.js : -1);
+    const bool special = (edge || has_src) && any_special(sp);
+    WarpChunk<Real> cs{};
+    bool wsrc = false;
+    int sbase = 0;
+    if (has_src) {
+        wsrc = __any_sync(kFull, sp.rs >= 0);
+        if (wsrc) {
+            cs.c0 = level_sample(pl.src, pl.src_stride, at.m0 + 1 + lane, prm.T);
+            cs.c1 = level_sample(pl.src, pl.src_stride, at.m0 + 33 + lane, prm.T);
+        }
+    }
+    // owned points that are interior grid points, in register indices
+    int ilo = 0, ihi = 0;
+    if (own) {
+        ilo = (int)(1 - gj <= 0 ? 0 : (1 - gj >= P ? P : 1 - gj));
+        ihi = (int)(nx - 1 - gj <= 0 ? 0 : (nx - 1 - gj >= P ? P : nx - 1 - gj));
+    }
+    const bool full_core = ilo == 0 && ihi == P;
+    const int rhi = own ? P : 0;  // probes: only the owner records
+    for (int s = 0; s < len; ++s) {
+        uint32_t lb[P];
+#pragma unroll
+        for (int c = 0; c < P / 8; ++c)
+            tmem_ld8(tm + (uint32_t)((len - 1 - s) * P + 8 * c), *reinterpret_cast<uint32_t(*)[8]>(lb + 8 * c));
+        Real lft, rgt;
+        warp_neighbours<Real, P>(l, lft, rgt, lane);
+        const int64_t m = at.m0 + s;
+        if (at.td.probe_end > at.td.probe_begin)
+            record_probes<Real, P>(l, lft, rgt, wabs, tb, 0, rhi, at.td.probe_begin, at.td.probe_end, prm.probes, m);
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < P / 8; ++c) tmem_wait_ld(*reinterpret_cast<uint32_t(*)[8]>(lb + 8 * c));
+        if (full_core) {
+#pragma unroll
+            for (int i = 0; i < P; ++i) racc = rfma(l[i], __uint_as_float(lb[i]), racc);
+        } else {
+#pragma unroll
+            for (int i = 0; i < P; ++i)
+                if (i >= ilo && i < ihi) racc = rfma(l[i], __uint_as_float(lb[i]), racc);
+        }
+        Real sval = Real(0);
+        if (wsrc) {
+            if (s - sbase == 32) {
+                sbase += 32;
+                cs.c0 = cs.c1;
+                cs.c1 = level_sample(pl.src, pl.src_stride, at.m0 + sbase + 33 + lane, prm.T);
+            }
+            sval = cs.get(s - sbase);
+        }
+        if (special) {
+            const Real uold = (FORM == kIncrement && sp.rs >= 0) ? reg_get<Real, P>(l, sp.rs) : Real(0);
+            leap_step<Real, FORM, P>(l, lw, lft, rgt, c2, kk);
+            patch_special<Real, FORM, P>(l, lw, sp, uold, sval, Real(0), Real(0), Real(0), Real(0));
+        } else {
+            leap_step<Real, FORM, P>(l, lw, lft, rgt, c2, kk);
+        }
+    }
+    if (own) {
+        regs_to_smem<Real, P>(out + 0 * W + tb, l);
+        regs_to_smem<Real, P>(out + 1 * W + tb, lw);
+    }
+    return racc;
+}
+
 // Sum of racc over the window's threads in a fixed order (warp shuffles, then
 // the warps in order); the result is valid in thread 0.
 template <int NT, int BAR>
@@ -381,9 +573,11 @@ struct AdjStage {
     int pad_;
 };
 
+// outb: where the compute threads leave the adjoint pair of stage y ([2][W] at
+// outb + 2 W y), or nullptr: back in the stage's adjoint windows.
 template <typename Real, int W>
 __device__ void adj_producer(const AdjParams<Real>& prm, Real* stage, uint64_t* full_bar, uint64_t* empty_bar,
-                             AdjStage<Real>* info)
+                             AdjStage<Real>* info, const Real* outb)
 {
     const unsigned long long total = (unsigned long long)prm.nspans * (unsigned long long)prm.ntiles;
     auto grab = [&]() -> long long {
@@ -466,10 +660,10 @@ __device__ void adj_producer(const AdjParams<Real>& prm, Real* stage, uint64_t* 
         const AdjStage<Real>& si = info[y];
         const int64_t dst = si.pu.base + (int64_t)si.td.local * prm.core;
         const uint32_t cbytes = (uint32_t)prm.core * sizeof(Real);
-        Real* st = stage + y * 4 * W;
+        const Real* src = outb ? outb + y * 2 * W : stage + y * 4 * W + 2 * W;
         const int out = (si.kp + 1) & 1;
-        bulk_store(prm.lq0[out] + dst, st + 2 * W + prm.H, cbytes);
-        bulk_store(prm.lq1[out] + dst, st + 3 * W + prm.H, cbytes);
+        bulk_store(prm.lq0[out] + dst, src + prm.H, cbytes);
+        bulk_store(prm.lq1[out] + dst, src + W + prm.H, cbytes);
         bulk_commit();
     };
     auto publish = [&](int y) {
@@ -550,17 +744,27 @@ __host__ __device__ constexpr int tmem_cols(int n)
     return c;
 }
 
-template <typename Real, int FORM, int P, int NT, int SA, bool TM>
+// Points of the CTA window: NT P, or with free warp windows of halo KH the
+// owned points of the warps plus the two halos.
+template <int P, int NT, int KH>
+__host__ __device__ constexpr int ws_window()
+{
+    return KH > 0 ? (NT / 32) * (32 * P - 2 * KH) + 2 * KH : NT * P;
+}
+
+template <typename Real, int FORM, int P, int NT, int SA, bool TM, int KH>
 __global__ void __launch_bounds__(NT + 32) adjoint_kernel_ws(const __grid_constant__ AdjParams<Real> prm)
 {
-    constexpr int W = NT * P;
+    constexpr int W = ws_window<P, NT, KH>();
     constexpr int NW = NT / 32;
     constexpr uint32_t NCOL = (uint32_t)tmem_cols(SA * P);
     static_assert(!TM || NCOL <= 512, "the Laplacian store exceeds the tensor memory of an SM");
+    static_assert(KH == 0 || TM, "free warp windows keep the Laplacians in TMEM");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Real* stage = reinterpret_cast<Real*>(smem_raw);  // [2 stages][4][W]
-    Real* laps = stage + 8 * W;                       // [SA][W] (not with TM)
-    Real* xch = laps + (TM ? 0 : SA * W);             // [2][NW][2]
+    Real* laps = stage + 8 * W;                       // [SA][W] (not with TM); with KH: [2 stages][2][W] out
+    Real* xch = laps + (TM ? 0 : SA * W);             // [2][NW][2] (not with KH)
+    Real* outb = KH > 0 ? laps : nullptr;
     __shared__ __align__(8) uint64_t full_bar[2];
     __shared__ __align__(8) uint64_t empty_bar[2];
     __shared__ __align__(16) AdjStage<Real> s_info[2];
@@ -588,7 +792,7 @@ __global__ void __launch_bounds__(NT + 32) adjoint_kernel_ws(const __grid_consta
     }
     __syncthreads();  // the last CTA-wide barrier: from here on only barrier 1 (compute threads)
     if (warp == NW) {
-        if (lane == 0) adj_producer<Real, W>(prm, stage, full_bar, empty_bar, s_info);
+        if (lane == 0) adj_producer<Real, W>(prm, stage, full_bar, empty_bar, s_info, outb);
         return;
     }
     uint32_t tm = 0;
@@ -614,7 +818,9 @@ __global__ void __launch_bounds__(NT + 32) adjoint_kernel_ws(const __grid_consta
         at.m0 = si.m0;
         at.len = si.len;
         Real* st = stage + y * 4 * W;
-        const Real racc = adj_tile<Real, FORM, P, NT, SA, NT, TM>(prm, at, st, laps, xch, buf, tm);
+        Real racc;
+        if constexpr (KH > 0) racc = adj_tile_fw<Real, FORM, P, NT, SA, KH>(prm, at, st, outb + y * 2 * W, tm);
+        else racc = adj_tile<Real, FORM, P, NT, SA, NT, TM>(prm, at, st, laps, xch, buf, tm);
         const double t = block_sum<NT, NT>((double)racc, red);
         if (tid == 0) prm.partial[(int64_t)(prm.nspans - 1 - si.kp) * prm.ntiles + si.tile] = t;
         fence_proxy_async_smem();
@@ -768,15 +974,17 @@ struct WsEntry {
     const void* fn;
     size_t smem;      // dynamic shared memory the kernel uses
     int tmem_cols;    // TMEM columns per CTA (0: Laplacians in shared memory)
+    int halo;         // the tile halo the kernel needs (free warp windows), 0: any
 };
 
-template <typename Real, int FORM, int P, int NT, int SA, bool TM>
+template <typename Real, int FORM, int P, int NT, int SA, bool TM, int KH = 0>
 WsEntry make_ws()
 {
-    constexpr int W = NT * P;
+    constexpr int W = ws_window<P, NT, KH>();
+    const size_t words = KH > 0 ? 12 * W : (8 + (TM ? 0 : SA)) * W + 4 * (NT / 32);
     return WsEntry{sizeof(Real) == 8 ? kF64 : kF32, FORM, W, SA, NT + 32,
-                   reinterpret_cast<const void*>(&adjoint_kernel_ws<Real, FORM, P, NT, SA, TM>),
-                   sizeof(Real) * ((8 + (TM ? 0 : SA)) * W + 4 * (NT / 32)), TM ? tmem_cols(SA * P) : 0};
+                   reinterpret_cast<const void*>(&adjoint_kernel_ws<Real, FORM, P, NT, SA, TM, KH>),
+                   sizeof(Real) * words, TM ? tmem_cols(SA * P) : 0, KH};
 }
 
 const WsEntry* ws_find(int dtype, int form)
@@ -784,8 +992,8 @@ const WsEntry* ws_find(int dtype, int form)
     static const WsEntry entries[] = {
         make_ws<double, kCanonical, 4, 128, 8, false>(),
         make_ws<double, kIncrement, 4, 128, 8, false>(),
-        make_ws<float, kIncrement, 8, 128, 16, true>(),
-        make_ws<float, kCanonical, 8, 128, 16, true>(),
+        make_ws<float, kIncrement, 8, 128, 16, true, 16>(),
+        make_ws<float, kCanonical, 8, 128, 16, true, 16>(),
     };
     for (const WsEntry& e : entries)
         if (e.dtype == dtype && e.form == form) return &e;
@@ -867,6 +1075,12 @@ int adj_ws_window(int dtype, int form)
 {
     const WsEntry* e = ws_find(dtype, form);
     return e ? e->W : 0;
+}
+
+int adj_ws_halo(int dtype, int form)
+{
+    const WsEntry* e = ws_find(dtype, form);
+    return e ? e->halo : 0;
 }
 
 cudaError_t adj_ws_prepare(int dtype, int form)

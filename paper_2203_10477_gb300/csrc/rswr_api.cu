@@ -1038,14 +1038,16 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     if (va < 0) return fail(RSWR_ENOTSUP, "no adjoint kernel for this dtype/form");
     const VariantInfo ai = adj_variant_info(va);
     const int SA = std::min(e->S, adj_variant_span(va));
-    const int H = (SA + 3) / 4 * 4;
+    // halo of both tilings: at least the span (rounded to 16 bytes of FP32);
+    // the persistent FP32 sweep's free warp windows ask for their own below
+    int H = (SA + 3) / 4 * 4;
     // the sweeps launch span by span or with tickets: a resident plan variant
     // gives way to the default one of its dtype and form
     const int vf = span_variant_info(e->variant).resident ? default_variant(e->dtype, e->form, SA) : e->variant;
     if (vf < 0) return fail(RSWR_ENOTSUP, "no span kernel variant for the adjoint sweep");
     const VariantInfo fi = span_variant_info(vf);
-    const int core_f = fi.W - 2 * H;
-    const int64_t pad = H + 8;
+    int core_f = fi.W - 2 * H;
+    int64_t pad = H + 8;
     const int64_t nspans = (T + SA - 1) / SA;
     auto up = [](size_t x) { return (x + 255) / 256 * 256; };
 
@@ -1090,13 +1092,25 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     // With every span state kept the whole adjoint sweep is one persistent launch
     // (its own window); otherwise one launch of the per-span kernel per span.
     const int w_ws = adj_ws_window(e->dtype, e->form);
-    bool use_ws = w_ws > 0 && adj_ws_span(e->dtype, e->form) >= SA && w_ws - 2 * H >= H;
+    const int h_ws = adj_ws_halo(e->dtype, e->form);  // 0: any halo >= the span
+    bool use_ws = w_ws > 0 && adj_ws_span(e->dtype, e->form) >= SA &&
+                  (h_ws > 0 ? h_ws >= H && fi.W - 2 * h_ws >= h_ws && w_ws - 2 * h_ws >= h_ws : w_ws - 2 * H >= H);
     if (core_f < H || ai.W - 2 * H < H) return fail(RSWR_EINVAL, "adjoint tiling: window too small");
+    const int H_span = H;
+    auto set_halo = [&](int h) {
+        H = h;
+        core_f = fi.W - 2 * H;
+        pad = H + 8;
+    };
     int64_t C;
     if (use_ws) {
+        if (h_ws > 0) set_halo(h_ws);
         make_layout(w_ws - 2 * H);
         C = spacing();
-        if (C != 1) use_ws = false;
+        if (C != 1) {
+            use_ws = false;
+            set_halo(H_span);
+        }
     }
     if (!use_ws) {
         make_layout(ai.W - 2 * H);

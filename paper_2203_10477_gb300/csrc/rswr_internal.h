@@ -204,6 +204,7 @@ cudaError_t adj_ws_occupancy(int dtype, int form, int* blocks_per_sm);
 cudaError_t adj_ws_launch(int dtype, int form, const void* params, int grid, cudaStream_t s);
 int adj_ws_span(int dtype, int form);    // span the persistent kernel's Laplacian store holds (0: none)
 int adj_ws_window(int dtype, int form);  // points per CTA window of the persistent kernel
+int adj_ws_halo(int dtype, int form);    // tile halo the persistent kernel needs (0: any halo >= the span)
 // lambda at level 1 of the reversed-time sweep: wbar[T] at j_r (interior receivers only)
 cudaError_t adj_init_launch(int dtype, int form, void* l0, void* l1, const void* prob_l, int nprob,
                             const void* wbar, int64_t T, cudaStream_t s);

@@ -462,14 +462,17 @@ def test_adjoint_grad_a_fp32(R, oracle_mod, spacing):
     assert np.linalg.norm(got - ref["dg"]) <= 1e-4 * np.linalg.norm(ref["dg"])
 
 
-def test_persistent_adjoint_equals_per_span_adjoint_bitwise(R):
-    """FP32: the persistent adjoint sweep (every span state kept, the
-    Laplacians in tensor memory) and the per-span launches of the checkpointed
-    path (Laplacians in shared memory) use the same tiles and do the same
-    operations in the same order, so their gradients agree bit for bit.
-    250 spans of 16 steps (the last one ragged), 8 tiles per span.  (In FP64
-    the two kernels tile the grid differently, so dL/da is summed in another
-    order there.)"""
+def test_persistent_adjoint_equals_per_span_adjoint(R, oracle_mod):
+    """FP32: the persistent adjoint sweep (every span state kept; free warp
+    windows, the Laplacians in tensor memory) and the per-span launches of the
+    checkpointed path (the warps of a tile exchange neighbours through shared
+    memory, Laplacians in shared memory) update every adjoint point with the
+    same operations on the same operands, so dL/dfA agrees bit for bit.  They
+    tile the grid differently (cores of 896 and 992 points), so the per-thread
+    FP32 sums of pairing terms meet in another order: dL/da is asserted to the
+    rounding of a 128-term FP32 sum (128 * 2^-24 of the sum of |terms|, taken
+    from the FP64 oracle).  250 spans of 16 steps (the last one ragged), 8 or 9
+    tiles per span."""
     dtype = F32
     nx, N, ov, T, jr = 8001, 8, 64, 4001, 2500
     a = 1.3
@@ -485,7 +488,8 @@ def test_persistent_adjoint_equals_per_span_adjoint_bitwise(R):
         out.append((host(res["grad_fA"]), res["grad_a"].item()))
     assert np.abs(out[0][0]).max() > 0 and out[0][1] != 0.0
     assert_bitwise(out[0][0], out[1][0], "grad_fA, persistent vs per-span")
-    assert out[0][1] == out[1][1], (out[0][1], out[1][1])
+    ref = oracle_mod.adjoint(nx, T, a, dt, g, np.zeros(T + 1), jr, w)
+    assert abs(out[0][1] - out[1][1]) <= 128 * 2.0 ** -24 * ref["abs_da"], (out[0][1], out[1][1], ref["abs_da"])
 
 
 @pytest.mark.parametrize("spacing", [0, 5])
