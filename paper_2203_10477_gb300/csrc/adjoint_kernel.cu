@@ -418,7 +418,20 @@ __device__ __forceinline__ Real adj_tile_fw(const AdjParams<Real>& prm, const Ad
         ihi = (int)(nx - 1 - gj <= 0 ? 0 : (nx - 1 - gj >= P ? P : nx - 1 - gj));
     }
     const bool full_core = ilo == 0 && ihi == P;
-    const int rhi = own ? P : 0;  // probes: only the owner records
+    // probes (dL/dfA samples): read once per tile; the owner thread of a
+    // probed point records it every level (more than two on one thread: the
+    // general path)
+    const int rhi = own ? P : 0;
+    OwnedProbe<Real> o0{}, o1{};
+    int nown = 0;
+    for (int q = at.td.probe_begin; q < at.td.probe_end; ++q) {
+        const int64_t li = prm.probes[q].gidx - wabs - (int64_t)tb;
+        if (li >= 0 && li < rhi) {
+            if (nown == 0) o0 = own_probe(prm.probes[q], wabs, tb, at.m0, len);
+            else if (nown == 1) o1 = own_probe(prm.probes[q], wabs, tb, at.m0, len);
+            ++nown;
+        }
+    }
     for (int s = 0; s < len; ++s) {
         uint32_t lb[P];
 #pragma unroll
@@ -426,9 +439,13 @@ __device__ __forceinline__ Real adj_tile_fw(const AdjParams<Real>& prm, const Ad
             tmem_ld8(tm + (uint32_t)((len - 1 - s) * P + 8 * c), *reinterpret_cast<uint32_t(*)[8]>(lb + 8 * c));
         Real lft, rgt;
         warp_neighbours<Real, P>(l, lft, rgt, lane);
-        const int64_t m = at.m0 + s;
-        if (at.td.probe_end > at.td.probe_begin)
-            record_probes<Real, P>(l, lft, rgt, wabs, tb, 0, rhi, at.td.probe_begin, at.td.probe_end, prm.probes, m);
+        if (nown > 2) {
+            record_probes<Real, P>(l, lft, rgt, wabs, tb, 0, rhi, at.td.probe_begin, at.td.probe_end, prm.probes,
+                                   at.m0 + s);
+        } else if (nown > 0) {
+            record_step<Real, P>(o0, l, lft, rgt, s);
+            if (nown > 1) record_step<Real, P>(o1, l, lft, rgt, s);
+        }
         __syncwarp();
 #pragma unroll
         for (int c = 0; c < P / 8; ++c) tmem_wait_ld(*reinterpret_cast<uint32_t(*)[8]>(lb + 8 * c));
