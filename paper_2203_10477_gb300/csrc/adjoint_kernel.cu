@@ -272,6 +272,86 @@ __device__ __forceinline__ Real adj_tile(const AdjParams<Real>& prm, const AdjTi
     return racc;
 }
 
+// Special-point patch of adj_tile_fw, applied after a step (the rules of
+// patch_special; the special points of one thread are distinct registers, so
+// the order in which they are patched does not matter).  The thread's end
+// registers are patched with predicated selects; a special point between them
+// takes one jump-table branch (reg_switch) instead of a tree of branches on
+// its register index.
+template <typename Real, int FORM, int P>
+__device__ __forceinline__ void patch_fast(Real (&u)[P], Real (&w)[P], const Special& sp, Real uold_s, Real sval,
+                                           Real fa_old, Real fa_new, Real fb_old, Real fb_new)
+{
+    auto at = [&](int i, Real& x, Real& y) {
+        if (sp.rs == i) {
+            if constexpr (FORM == kIncrement) {
+                y = radd(y, sval);
+                x = radd(uold_s, y);
+            } else {
+                x = radd(x, sval);
+            }
+        }
+        if (sp.r0 == i) {
+            x = fa_new;
+            if constexpr (FORM == kIncrement) y = rsub(fa_new, fa_old);
+        }
+        if (sp.rm == i) x = y = Real(0);
+        if (sp.r1 == i) {
+            x = fb_new;
+            if constexpr (FORM == kIncrement) y = rsub(fb_new, fb_old);
+        }
+        if (sp.rp == i) x = y = Real(0);
+    };
+    at(0, u[0], w[0]);
+    at(P - 1, u[P - 1], w[P - 1]);
+    auto one = [&](int r) {
+        if (r > 0 && r < P - 1)
+            reg_switch<P>(r, [&](auto I) {
+                constexpr int i = decltype(I)::value;
+                at(i, u[i], w[i]);
+            });
+    };
+    one(sp.rs);
+    one(sp.r0);
+    one(sp.rm);
+    one(sp.r1);
+    one(sp.rp);
+}
+
+// u[r] for a register index known at run time (one jump-table branch).
+template <typename Real, int P>
+__device__ __forceinline__ Real reg_get_sw(const Real (&u)[P], int r)
+{
+    Real v = u[0];
+    if (r == P - 1) v = u[P - 1];
+    else if (r > 0) reg_switch<P>(r, [&](auto I) { v = u[decltype(I)::value]; });
+    return v;
+}
+
+// The probe sample of level n0 + s (record_step with a jump table).
+template <typename Real, int P>
+__device__ __forceinline__ void record_sw(OwnedProbe<Real>& o, const Real (&u)[P], Real lft, Real rgt, int s)
+{
+    if (s < o.count) {
+        Real um = lft, uc = u[0], up = u[1];
+        if (o.r == P - 1) {
+            um = u[P - 2];
+            uc = u[P - 1];
+            up = rgt;
+        } else if (o.r > 0) {
+            reg_switch<P>(o.r, [&](auto I) {
+                constexpr int i = decltype(I)::value;
+                um = u[i - 1];
+                uc = u[i];
+                up = u[i + 1];
+            });
+        }
+        const Real val = (o.kind == 0) ? uc : rsub(up, um);
+        *o.ptr = rmul(val, o.scale);
+        o.ptr += o.stride;
+    }
+}
+
 // The same tile with free warp windows (FP32, Laplacians in TMEM).  Warp w
 // works on the 32 P points of the tile window from w (32 P - 2 KH) on and owns
 // the middle 32 P - 2 KH of them; its neighbours come from shuffles only, with
@@ -292,6 +372,7 @@ __device__ __forceinline__ Real adj_tile_fw(const AdjParams<Real>& prm, const Ad
     constexpr int W = NW * WO + 2 * KH;  // tile window
     static_assert(sizeof(Real) == 4 && P % 8 == 0 && NT == 128, "TMEM store: FP32, 8-column chunks, 4 warps");
     static_assert(KH % P == 0 && KH >= SA && WO > 0, "warp halo: whole threads, at least one span long");
+    static_assert(SA <= 31, "the samples of a span are held across one warp");
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
@@ -314,20 +395,25 @@ __device__ __forceinline__ Real adj_tile_fw(const AdjParams<Real>& prm, const Ad
         smem_to_regs<Real, P>(stage + 0 * W + tb, u);
         smem_to_regs<Real, P>(stage + 1 * W + tb, w);
         const Special sp = make_special<P>(gj, nx, -1);
-        const bool special = edge && any_special(sp);
-        WarpChunk<Real> ca{}, cb{};
+        // warp-uniform: every lane of a warp that holds a special point runs the
+        // patch (its selects leave the other lanes' points alone), so that the
+        // level loop is not split into a patched and a plain copy that the
+        // warp would run one after the other
+        const bool special = __any_sync(kFull, edge && any_special(sp));
+        // the Dirichlet samples of levels n0 .. n0+31 across the warp (len <= 31:
+        // one shuffle per level), the previous level's carried in a register
+        Real ca = Real(0), cb = Real(0), fa_old = Real(0), fb_old = Real(0);
         bool wa = false, wb = false;
-        int cbase = 0;
         if (edge) {
             wa = __any_sync(kFull, sp.r0 >= 0) && pu.fA != nullptr;
             wb = __any_sync(kFull, sp.r1 >= 0) && pu.fB != nullptr;
             if (wa) {
-                ca.c0 = level_sample(pu.fA, 1, at.n0 + lane, prm.T);
-                ca.c1 = level_sample(pu.fA, 1, at.n0 + 32 + lane, prm.T);
+                ca = level_sample(pu.fA, 1, at.n0 + lane, prm.T);
+                fa_old = __shfl_sync(kFull, ca, 0);
             }
             if (wb) {
-                cb.c0 = level_sample(pu.fB, 1, at.n0 + lane, prm.T);
-                cb.c1 = level_sample(pu.fB, 1, at.n0 + 32 + lane, prm.T);
+                cb = level_sample(pu.fB, 1, at.n0 + lane, prm.T);
+                fb_old = __shfl_sync(kFull, cb, 0);
             }
         }
         auto level = [&](auto step_c, int s) {
@@ -369,24 +455,11 @@ __device__ __forceinline__ Real adj_tile_fw(const AdjParams<Real>& prm, const Ad
             for (int c = 0; c < P / 8; ++c)
                 tmem_st8(tm + (uint32_t)(s * P + 8 * c), *reinterpret_cast<const uint32_t(*)[8]>(b + 8 * c));
             if constexpr (STEP) {
-                if (s - cbase == 32) {
-                    cbase += 32;
-                    ca.c0 = ca.c1;
-                    cb.c0 = cb.c1;
-                    if (wa) ca.c1 = level_sample(pu.fA, 1, at.n0 + cbase + 32 + lane, prm.T);
-                    if (wb) cb.c1 = level_sample(pu.fB, 1, at.n0 + cbase + 32 + lane, prm.T);
-                }
-                Real fa_old = Real(0), fa_new = Real(0), fb_old = Real(0), fb_new = Real(0);
-                if (wa) {
-                    fa_old = ca.get(s - cbase);
-                    fa_new = ca.get(s - cbase + 1);
-                }
-                if (wb) {
-                    fb_old = cb.get(s - cbase);
-                    fb_new = cb.get(s - cbase + 1);
-                }
-                if (special)
-                    patch_special<Real, FORM, P>(u, w, sp, Real(0), Real(0), fa_old, fa_new, fb_old, fb_new);
+                const Real fa_new = wa ? __shfl_sync(kFull, ca, s + 1) : Real(0);
+                const Real fb_new = wb ? __shfl_sync(kFull, cb, s + 1) : Real(0);
+                if (special) patch_fast<Real, FORM, P>(u, w, sp, Real(0), Real(0), fa_old, fa_new, fb_old, fb_new);
+                fa_old = fa_new;
+                fb_old = fb_new;
             }
         };
         for (int s = 0; s + 1 < len; ++s) level(std::true_type{}, s);
@@ -400,16 +473,13 @@ __device__ __forceinline__ Real adj_tile_fw(const AdjParams<Real>& prm, const Ad
     smem_to_regs<Real, P>(stage + 2 * W + tb, l);
     smem_to_regs<Real, P>(stage + 3 * W + tb, lw);
     const Special sp = make_special<P>(gj, nx, has_src ? pl.js : -1);
-    const bool special = (edge || has_src) && any_special(sp);
-    WarpChunk<Real> cs{};
+    const bool special = __any_sync(kFull, (edge || has_src) && any_special(sp));  // warp-uniform, as above
+    // the source samples of levels m0+1 .. m0+32 across the warp
+    Real cs = Real(0);
     bool wsrc = false;
-    int sbase = 0;
     if (has_src) {
         wsrc = __any_sync(kFull, sp.rs >= 0);
-        if (wsrc) {
-            cs.c0 = level_sample(pl.src, pl.src_stride, at.m0 + 1 + lane, prm.T);
-            cs.c1 = level_sample(pl.src, pl.src_stride, at.m0 + 33 + lane, prm.T);
-        }
+        if (wsrc) cs = level_sample(pl.src, pl.src_stride, at.m0 + 1 + lane, prm.T);
     }
     // owned points that are interior grid points, in register indices
     int ilo = 0, ihi = 0;
@@ -422,16 +492,16 @@ __device__ __forceinline__ Real adj_tile_fw(const AdjParams<Real>& prm, const Ad
     // probed point records it every level (more than two on one thread: the
     // general path)
     const int rhi = own ? P : 0;
-    OwnedProbe<Real> o0{}, o1{};
+    OwnedProbe<Real> o0{};  // count 0: records nothing
     int nown = 0;
     for (int q = at.td.probe_begin; q < at.td.probe_end; ++q) {
         const int64_t li = prm.probes[q].gidx - wabs - (int64_t)tb;
         if (li >= 0 && li < rhi) {
             if (nown == 0) o0 = own_probe(prm.probes[q], wabs, tb, at.m0, len);
-            else if (nown == 1) o1 = own_probe(prm.probes[q], wabs, tb, at.m0, len);
             ++nown;
         }
     }
+    nown = __reduce_max_sync(kFull, nown);  // warp-uniform: the owner records, the other lanes pass
     for (int s = 0; s < len; ++s) {
         uint32_t lb[P];
 #pragma unroll
@@ -439,13 +509,11 @@ __device__ __forceinline__ Real adj_tile_fw(const AdjParams<Real>& prm, const Ad
             tmem_ld8(tm + (uint32_t)((len - 1 - s) * P + 8 * c), *reinterpret_cast<uint32_t(*)[8]>(lb + 8 * c));
         Real lft, rgt;
         warp_neighbours<Real, P>(l, lft, rgt, lane);
-        if (nown > 2) {
+        if (nown > 1)
             record_probes<Real, P>(l, lft, rgt, wabs, tb, 0, rhi, at.td.probe_begin, at.td.probe_end, prm.probes,
                                    at.m0 + s);
-        } else if (nown > 0) {
-            record_step<Real, P>(o0, l, lft, rgt, s);
-            if (nown > 1) record_step<Real, P>(o1, l, lft, rgt, s);
-        }
+        else if (nown > 0)
+            record_sw<Real, P>(o0, l, lft, rgt, s);
         __syncwarp();
 #pragma unroll
         for (int c = 0; c < P / 8; ++c) tmem_wait_ld(*reinterpret_cast<uint32_t(*)[8]>(lb + 8 * c));
@@ -457,22 +525,11 @@ __device__ __forceinline__ Real adj_tile_fw(const AdjParams<Real>& prm, const Ad
             for (int i = 0; i < P; ++i)
                 if (i >= ilo && i < ihi) racc = rfma(l[i], __uint_as_float(lb[i]), racc);
         }
-        Real sval = Real(0);
-        if (wsrc) {
-            if (s - sbase == 32) {
-                sbase += 32;
-                cs.c0 = cs.c1;
-                cs.c1 = level_sample(pl.src, pl.src_stride, at.m0 + sbase + 33 + lane, prm.T);
-            }
-            sval = cs.get(s - sbase);
-        }
-        if (special) {
-            const Real uold = (FORM == kIncrement && sp.rs >= 0) ? reg_get<Real, P>(l, sp.rs) : Real(0);
-            leap_step<Real, FORM, P>(l, lw, lft, rgt, c2, kk);
-            patch_special<Real, FORM, P>(l, lw, sp, uold, sval, Real(0), Real(0), Real(0), Real(0));
-        } else {
-            leap_step<Real, FORM, P>(l, lw, lft, rgt, c2, kk);
-        }
+        const Real sval = wsrc ? __shfl_sync(kFull, cs, s) : Real(0);
+        Real uold = Real(0);  // the level-m value at the source (increment form)
+        if (FORM == kIncrement && special) uold = reg_get_sw<Real, P>(l, sp.rs);
+        leap_step<Real, FORM, P>(l, lw, lft, rgt, c2, kk);
+        if (special) patch_fast<Real, FORM, P>(l, lw, sp, uold, sval, Real(0), Real(0), Real(0), Real(0));
     }
     if (own) {
         regs_to_smem<Real, P>(out + 0 * W + tb, l);
