@@ -318,6 +318,42 @@ __device__ __forceinline__ void patch_fast(Real (&u)[P], Real (&w)[P], const Spe
     one(sp.rp);
 }
 
+// The patch when every special point of the thread sits on an end register in
+// the usual way: the left node on register 0 with the outside point j = -1 on
+// the previous thread's last register, the right node on register P-1 with
+// j = nx on the next thread's register 0, and no source (the persistent
+// sweep's tiles start on multiples of P, so the left side always looks like
+// this, and the right side whenever nx is a multiple of P).  Selects only;
+// fixed_ends() tells whether it applies to a thread.
+struct EndPatch {
+    bool a0, z0, bl, zl;  // register 0: left node / outside; register P-1: right node / outside
+};
+
+template <int P>
+__device__ __forceinline__ bool fixed_ends(const Special& sp)
+{
+    return sp.rs < 0 && (sp.r0 == -1 || sp.r0 == 0) && (sp.rm == -1 || sp.rm == P - 1) &&
+           (sp.r1 == -1 || sp.r1 == P - 1) && (sp.rp == -1 || sp.rp == 0);
+}
+
+template <typename Real, int FORM, int P>
+__device__ __forceinline__ void patch_ends(Real (&u)[P], Real (&w)[P], const EndPatch& ep, Real fa_old, Real fa_new,
+                                           Real fb_old, Real fb_new)
+{
+    if constexpr (FORM == kIncrement) {
+        const Real da = rsub(fa_new, fa_old), db = rsub(fb_new, fb_old);
+        u[0] = ep.a0 ? fa_new : (ep.z0 ? Real(0) : u[0]);
+        w[0] = ep.a0 ? da : (ep.z0 ? Real(0) : w[0]);
+        u[P - 1] = ep.bl ? fb_new : (ep.zl ? Real(0) : u[P - 1]);
+        w[P - 1] = ep.bl ? db : (ep.zl ? Real(0) : w[P - 1]);
+    } else {
+        u[0] = ep.a0 ? fa_new : (ep.z0 ? Real(0) : u[0]);
+        w[0] = ep.z0 ? Real(0) : w[0];
+        u[P - 1] = ep.bl ? fb_new : (ep.zl ? Real(0) : u[P - 1]);
+        w[P - 1] = ep.zl ? Real(0) : w[P - 1];
+    }
+}
+
 // u[r] for a register index known at run time (one jump-table branch).
 template <typename Real, int P>
 __device__ __forceinline__ Real reg_get_sw(const Real (&u)[P], int r)
@@ -334,7 +370,11 @@ __device__ __forceinline__ void record_sw(OwnedProbe<Real>& o, const Real (&u)[P
 {
     if (s < o.count) {
         Real um = lft, uc = u[0], up = u[1];
-        if (o.r == P - 1) {
+        if (o.r == 1) {  // the boundary-gradient probe (j = 1 on a tile that starts on a multiple of P)
+            um = u[0];
+            uc = u[1];
+            up = u[2];
+        } else if (o.r == P - 1) {
             um = u[P - 2];
             uc = u[P - 1];
             up = rgt;
@@ -400,6 +440,9 @@ __device__ __forceinline__ Real adj_tile_fw(const AdjParams<Real>& prm, const Ad
         // level loop is not split into a patched and a plain copy that the
         // warp would run one after the other
         const bool special = __any_sync(kFull, edge && any_special(sp));
+        // end registers only, in every lane of the warp: the select patch
+        const bool ends = special && __all_sync(kFull, fixed_ends<P>(sp));
+        const EndPatch ep{sp.r0 == 0, sp.rp == 0, sp.r1 == P - 1, sp.rm == P - 1};
         // the Dirichlet samples of levels n0 .. n0+31 across the warp (len <= 31:
         // one shuffle per level), the previous level's carried in a register
         Real ca = Real(0), cb = Real(0), fa_old = Real(0), fb_old = Real(0);
@@ -457,7 +500,8 @@ __device__ __forceinline__ Real adj_tile_fw(const AdjParams<Real>& prm, const Ad
             if constexpr (STEP) {
                 const Real fa_new = wa ? __shfl_sync(kFull, ca, s + 1) : Real(0);
                 const Real fb_new = wb ? __shfl_sync(kFull, cb, s + 1) : Real(0);
-                if (special) patch_fast<Real, FORM, P>(u, w, sp, Real(0), Real(0), fa_old, fa_new, fb_old, fb_new);
+                if (ends) patch_ends<Real, FORM, P>(u, w, ep, fa_old, fa_new, fb_old, fb_new);
+                else if (special) patch_fast<Real, FORM, P>(u, w, sp, Real(0), Real(0), fa_old, fa_new, fb_old, fb_new);
                 fa_old = fa_new;
                 fb_old = fb_new;
             }
@@ -474,6 +518,8 @@ __device__ __forceinline__ Real adj_tile_fw(const AdjParams<Real>& prm, const Ad
     smem_to_regs<Real, P>(stage + 3 * W + tb, lw);
     const Special sp = make_special<P>(gj, nx, has_src ? pl.js : -1);
     const bool special = __any_sync(kFull, (edge || has_src) && any_special(sp));  // warp-uniform, as above
+    const bool ends = special && __all_sync(kFull, fixed_ends<P>(sp));
+    const EndPatch ep{sp.r0 == 0, sp.rp == 0, sp.r1 == P - 1, sp.rm == P - 1};
     // the source samples of levels m0+1 .. m0+32 across the warp
     Real cs = Real(0);
     bool wsrc = false;
@@ -527,9 +573,10 @@ __device__ __forceinline__ Real adj_tile_fw(const AdjParams<Real>& prm, const Ad
         }
         const Real sval = wsrc ? __shfl_sync(kFull, cs, s) : Real(0);
         Real uold = Real(0);  // the level-m value at the source (increment form)
-        if (FORM == kIncrement && special) uold = reg_get_sw<Real, P>(l, sp.rs);
+        if (FORM == kIncrement && special && !ends) uold = reg_get_sw<Real, P>(l, sp.rs);
         leap_step<Real, FORM, P>(l, lw, lft, rgt, c2, kk);
-        if (special) patch_fast<Real, FORM, P>(l, lw, sp, uold, sval, Real(0), Real(0), Real(0), Real(0));
+        if (ends) patch_ends<Real, FORM, P>(l, lw, ep, Real(0), Real(0), Real(0), Real(0));
+        else if (special) patch_fast<Real, FORM, P>(l, lw, sp, uold, sval, Real(0), Real(0), Real(0), Real(0));
     }
     if (own) {
         regs_to_smem<Real, P>(out + 0 * W + tb, l);
