@@ -462,7 +462,8 @@ def test_adjoint_grad_a_fp32(R, oracle_mod, spacing):
     assert np.linalg.norm(got - ref["dg"]) <= 1e-4 * np.linalg.norm(ref["dg"])
 
 
-def test_persistent_adjoint_equals_per_span_adjoint(R, oracle_mod):
+@pytest.mark.parametrize("nx", [8001, 8192])
+def test_persistent_adjoint_equals_per_span_adjoint(R, oracle_mod, nx):
     """FP32: the persistent adjoint sweep (every span state kept; free warp
     windows, the Laplacians in tensor memory) and the per-span launches of the
     checkpointed path (the warps of a tile exchange neighbours through shared
@@ -471,10 +472,12 @@ def test_persistent_adjoint_equals_per_span_adjoint(R, oracle_mod):
     tile the grid differently (cores of 896 and 992 points), so the per-thread
     FP32 sums of pairing terms meet in another order: dL/da is asserted to the
     rounding of a 128-term FP32 sum (128 * 2^-24 of the sum of |terms|, taken
-    from the FP64 oracle).  250 spans of 16 steps (the last one ragged), 8 or 9
-    tiles per span."""
+    from the FP64 oracle).  250 spans of 16 steps (the last one ragged), 8 to
+    10 tiles per span.  nx = 8192 puts the right node on a thread's last
+    register (the persistent kernel's select patch), nx = 8001 on its first
+    (the general patch)."""
     dtype = F32
-    nx, N, ov, T, jr = 8001, 8, 64, 4001, 2500
+    N, ov, T, jr = 8, 64, 4001, 2500
     a = 1.3
     dt = 0.9 / (nx - 1) / a
     g = inputs.lowpass_noise(T, seed=4)
@@ -490,6 +493,40 @@ def test_persistent_adjoint_equals_per_span_adjoint(R, oracle_mod):
     assert_bitwise(out[0][0], out[1][0], "grad_fA, persistent vs per-span")
     ref = oracle_mod.adjoint(nx, T, a, dt, g, np.zeros(T + 1), jr, w)
     assert abs(out[0][1] - out[1][1]) <= 128 * 2.0 ** -24 * ref["abs_da"], (out[0][1], out[1][1], ref["abs_da"])
+
+
+def test_batch_adjoint_with_grad_a_fp32(R, oracle_mod):
+    """FP32 batch of uneven problems with dL/da (the persistent adjoint sweep
+    with its tensor-memory store over several problems' tiles): every
+    problem's dL/dfA is bit for bit the one a single-problem plan gives, and
+    both gradients are within the FP32 tolerances of the FP64 oracle."""
+    r = inputs.rng(27)
+    T = 500
+    probs, jrs = [], []
+    for i in range(4):
+        nx = int(r.integers(900, 7000))
+        a = float(r.uniform(0.5, 2.0))
+        dt = inputs.dt_for_cfl(nx, a, 0.8)
+        probs.append(inputs.Problem(nx, a, dt, T, max(1, nx // 1024), 32, inputs.lowpass_noise(T, seed=40 + i),
+                                    np.zeros(T + 1)))
+        # well inside the reach of the boundary waveform (0.8 points per step),
+        # so that every gradient is far above FP32's rounding
+        jrs.append(int(r.integers(1, T // 3)))
+    b = R.Batch(probs, dtype=F32)
+    fA = np.concatenate([p.fA for p in probs])
+    w = inputs.rng(28).standard_normal((len(probs), T + 1))
+    res = b.adjoint(fA, None, T, jrs, w, want_a=True)
+    b.check()
+    gf = host(res["grad_fA"])
+    ga = host(res["grad_a"])
+    for i, p in enumerate(probs):
+        plan = R.Plan(0.0, 1.0, p.a, p.nx, p.dt, p.n_sub, p.overlap, dtype=F32)
+        single = plan.adjoint(p.fA, None, T, jrs[i], w[i], want_a=True)
+        assert_bitwise(gf[i], host(single["grad_fA"]), f"problem {i} grad_fA, batch vs single plan")
+        ref = oracle_mod.adjoint(p.nx, T, p.a, p.dt, p.fA, p.fB, jrs[i], w[i])
+        got = gf[i].astype(np.float64)
+        assert np.linalg.norm(got - ref["dg"]) <= 1e-4 * np.linalg.norm(ref["dg"]), i
+        assert abs(ga[i] - ref["da"]) <= 1e-4 * ref["abs_da"], (i, ga[i], ref["da"])
 
 
 @pytest.mark.parametrize("spacing", [0, 5])
