@@ -1042,10 +1042,13 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     // the persistent FP32 sweep's free warp windows ask for their own below
     int H = (SA + 3) / 4 * 4;
     // the sweeps launch span by span or with tickets: a resident plan variant
-    // gives way to the default one of its dtype and form
-    const int vf = span_variant_info(e->variant).resident ? default_variant(e->dtype, e->form, SA) : e->variant;
+    // gives way to the default one of its dtype and form (but runs the
+    // checkpoint sweep itself when every span state is kept; below)
+    const VariantInfo vplan = span_variant_info(e->variant);
+    const int v_default = default_variant(e->dtype, e->form, SA);
+    int vf = vplan.resident ? v_default : e->variant;
     if (vf < 0) return fail(RSWR_ENOTSUP, "no span kernel variant for the adjoint sweep");
-    const VariantInfo fi = span_variant_info(vf);
+    VariantInfo fi = span_variant_info(vf);
     int core_f = fi.W - 2 * H;
     int64_t pad = H + 8;
     const int64_t nspans = (T + SA - 1) / SA;
@@ -1115,6 +1118,39 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     if (!use_ws) {
         make_layout(ai.W - 2 * H);
         C = spacing();
+    }
+    // A resident plan variant runs the checkpoint sweep when every span state
+    // is kept (one launch, the tile windows on chip, each span's core written
+    // out) and the sweep's tiles all fit on the GPU at once: on small grids the
+    // ticketed sweep is paced by one tile's chain per span.
+    bool res_sweep = false;
+    if (vplan.resident && use_ws && C == 1 && variant_takes_span(vplan, SA) && vplan.W - 2 * H >= H) {
+        const int core_r = vplan.W - 2 * H;
+        int64_t ntr = 0;
+        for (int p = 0; p < np; ++p) ntr += (e->probs[p].nx + core_r - 1) / core_r;
+        int bps_r = 0;
+        RSWR_CUDA(span_occupancy(e->variant, &bps_r));
+        if ((int64_t)bps_r * e->num_sms >= ntr) {
+            vf = e->variant;
+            fi = vplan;
+            core_f = core_r;
+            make_layout(w_ws - 2 * H);
+            C = spacing();
+            res_sweep = C == 1;
+            if (!res_sweep) {
+                vf = v_default;
+                fi = span_variant_info(vf);
+                core_f = fi.W - 2 * H;
+                make_layout(w_ws - 2 * H);
+                C = spacing();
+                if (C != 1) {
+                    use_ws = false;
+                    set_halo(H_span);
+                    make_layout(ai.W - 2 * H);
+                    C = spacing();
+                }
+            }
+        }
     }
     if (keep && C != 1) return fail(RSWR_ENOMEM, "the span states of this run do not fit in device memory");
     const int64_t nck = std::max<int64_t>(1, (nspans + C - 1) / C);
@@ -1294,7 +1330,33 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
     if (!reuse) {
     RSWR_CUDA(cudaMemsetAsync(state0(CK0), 0, 2 * arr, s));
     RSWR_CUDA(set_boundary_launch(e->dtype, e->form, state0(CK0), state1(CK0), d_pu, np, s));
-    if (C == 1 && last_ck_span > 0) {
+    if (res_sweep && (keep ? nspans : last_ck_span) > 0) {
+        // resident tiles: one cooperative launch over every span of the sweep
+        // (a kept forward run: all of them, the final state into state nspans)
+        SpanParams<Real> cp = fp;
+        cp.span = -1;
+        cp.nspans = (int32_t)(keep ? nspans : last_ck_span);
+        cp.ck_stride = (int64_t)(2 * arr / es);
+        cp.q0[0] = state0(CK0);
+        cp.q1[0] = state1(CK0);
+        cp.q0[1] = cp.q1[1] = nullptr;
+        cp.done = d_done;
+        const size_t xb = es * 8 * (size_t)H * (size_t)ntf;
+        if (xb > e->xbuf_cap) {
+            RSWR_CUDA(cudaStreamSynchronize(s));
+            cudaFree(e->d_xbuf);
+            e->d_xbuf = nullptr;
+            e->xbuf_cap = 0;
+            if (cudaMalloc(&e->d_xbuf, xb) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(RSWR_ENOMEM, "halo exchange slots");
+            }
+            e->xbuf_cap = xb;
+        }
+        cp.xbuf = static_cast<Real*>(e->d_xbuf);
+        RSWR_CUDA(cudaMemsetAsync(d_done, 0, sizeof(int) * ntf, s));
+        RSWR_CUDA(span_launch(vf, &cp, (int)ntf, s));
+    } else if (C == 1 && last_ck_span > 0) {
         // every span state is kept: the whole sweep is one persistent launch in
         // which span k reads state k and writes state k + 1 (neighbour flags as in
         // rswr_run; the states are distinct arrays, so only read-after-write waits)
@@ -1332,7 +1394,12 @@ rswr_status adjoint_full(Engine* e, int64_t T, const int64_t* j_r, const void* f
         // last level, the final state pair
         Real* f0 = state0(CK0);
         Real* f1 = state1(CK0);
-        if (nspans > 0) {
+        if (res_sweep && nspans > 0) {
+            // the resident sweep ran every span: the final state is state nspans
+            // (the segment slot, unused when every span state is kept)
+            f0 = state0(CK0 + nspans);
+            f1 = state1(CK0 + nspans);
+        } else if (nspans > 0) {
             const int64_t k = nspans - 1;  // C == 1: state k is checkpoint k
             rswr_status st = forward_span(k, state0(CK0 + k), state1(CK0 + k), state0(WK0), state1(WK0));
             if (st != RSWR_OK) return st;

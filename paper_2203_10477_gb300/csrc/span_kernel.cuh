@@ -999,6 +999,17 @@ __global__ void __launch_bounds__(NT, MINB) span_kernel_res(const __grid_constan
         owned_to_smem<Real, P, KH>(sw + tb, w, own_lo, own_hi);
         __syncthreads();
         if (k + 1 == prm.nspans) break;
+        if (prm.ck_stride) {
+            // every span state kept (the adjoint's checkpoint sweep): the core
+            // of level n0 + steps into state k + 1 (the last one after the loop)
+            const int64_t dst = pr.base + (int64_t)td.local * prm.core;
+            Real* d0 = span_state(prm, 0, k + 1) + dst;
+            Real* d1 = span_state(prm, 1, k + 1) + dst;
+            for (int i = tid; i < prm.core; i += NT) {
+                d0[i] = su[H + i];
+                d1[i] = sw[H + i];
+            }
+        }
 
         // strips out: the first and last H core points, both components
         const int par = k & 1;

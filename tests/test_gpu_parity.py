@@ -998,6 +998,46 @@ def test_run_keep_equals_run_and_the_adjoint_reuses_it(R, oracle_mod, dtype, nx,
         assert abs(float(got["grad_a"][0]) - o["da"]) <= 1e-12 * o["abs_da"]
 
 
+@pytest.mark.parametrize("dtype", [F32, F64])
+def test_resident_checkpoint_sweep_equals_the_ticketed_one(R, oracle_mod, dtype):
+    """A plan on a resident variant runs the adjoint's checkpoint sweep (every
+    span state kept) as one resident launch that writes each span's core; the
+    gradients, and a kept forward run (its state, receiver trace and the
+    gradient that reuses it), equal those of a plan on the default variant
+    bit for bit (the adjoint tiling is the same, so dL/da is summed in the
+    same order).  63 spans, the last one ragged."""
+    nx, N, ov, T, jr = 20001, 8, 64, 1001, 700
+    a = 1.3
+    dt = 0.9 / (nx - 1) / a
+    g = inputs.lowpass_noise(T, seed=12)
+    w = inputs.rng(13).standard_normal(T + 1)
+    res_v = [v for v in R.variants() if v["dtype"] == dtype and v["resident"]]
+    assert res_v
+    ref_plan = R.Plan(0.0, 1.0, a, nx, dt, N, ov, dtype=dtype)
+    ref = ref_plan.adjoint(g, None, T, jr, w, want_a=True)
+    ref_keep = ref_plan.run_keep(g, None, T, j_r=jr)
+    ref_after = ref_plan.adjoint(g, None, T, jr, w, want_a=True)
+    ref_plan.check()
+    assert float(ref["grad_fA"].abs().max()) > 0
+    for v in res_v:
+        plan = R.Plan(0.0, 1.0, a, nx, dt, N, ov, dtype=dtype)
+        plan.set_span(min(32, v["max_span"] or 32))
+        plan.set_variant(v["variant"])
+        got = plan.adjoint(g, None, T, jr, w, want_a=True)
+        plan.check()
+        what = f"variant {v['variant']}"
+        assert_bitwise(host(got["grad_fA"]), host(ref["grad_fA"]), what + " grad_fA")
+        assert got["grad_a"].item() == ref["grad_a"].item(), what
+        kept = plan.run_keep(g, None, T, j_r=jr)
+        plan.check()
+        for k in ("u", "w", "recv"):
+            assert_bitwise(host(kept[k]), host(ref_keep[k]), f"{what} kept run {k}")
+        after = plan.adjoint(g, None, T, jr, w, want_a=True)
+        plan.check()
+        assert_bitwise(host(after["grad_fA"]), host(ref_after["grad_fA"]), what + " grad_fA after keep")
+        assert after["grad_a"].item() == ref_after["grad_a"].item(), what
+
+
 def test_adjoint_after_run_keep_with_other_inputs_sweeps_again(R, oracle_mod):
     """Other boundary samples (another pointer) than the kept run's: the adjoint
     does its own forward sweep and matches the oracle for its own inputs."""
