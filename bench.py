@@ -592,6 +592,10 @@ def profile_case(which: str, variant=None, span=None, full=False, log2_nx=22) ->
         dtype = rswr.F64 if which == "adj64" else rswr.F32
         td = torch.float64 if dtype == rswr.F64 else torch.float32
         plan = rswr.Plan.from_problem(p, dtype=dtype)
+        if span is not None:
+            plan.set_span(span)
+        if variant is not None:
+            plan.set_variant(variant)  # e.g. the resident variant the bench's autotuner picks on c4
         fA = torch.as_tensor(p.fA, device="cuda").to(td)
         w = torch.as_tensor(inputs.lowpass_noise(p.T, seed=4), device="cuda").to(td)
         for _ in range(2):
