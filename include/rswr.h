@@ -259,7 +259,10 @@ rswr_status rswr_run_host(rswr_plan_t plan, const void* fA, const void* fB, int6
  * (the flux round trip g = (u+ - u-)/(2dx), ghost = u + 2dx g).
  * Same arguments as rswr_run (no traces or receiver); spans (host, capacity
  * spans_cap, may be NULL) receives the selected spans, *nspans their count.
- * Synchronous (the host reads every selected span). */
+ * Synchronous.  The span is chosen on the device: the call queues the kernels
+ * of as many spans as the run needs at the least (each span advances at most
+ * the Theorem's cap), reads the run's progress back, and repeats until T is
+ * reached — usually one read-back per run. */
 rswr_status rswr_run_paper(rswr_plan_t plan, const void* fA, const void* fB, int64_t T, const void* q0,
                            const void* q1, void* out0, void* out1, int64_t* spans, int64_t spans_cap,
                            int64_t* nspans, void* stream);

@@ -11,15 +11,20 @@
 //       the largest number of leading steps over which they agree exactly at
 //       some overlap point; the global span is the minimum over pairs (Sec. 3,
 //       atomicMin).
-//   host: caps the span by the Waveform Time Span Theorem (Sec. 2.4).
+//   paper_select_kernel: caps the span by the Waveform Time Span Theorem
+//       (Sec. 2.4), records it, and copies the span's boundary samples for the
+//       span kernel.
 //   rswr_resolve_kernel (tiles of each subdomain's part of the combined
 //       solution, Sec. 2.5): solves the subdomain again over the span with
 //       its input flux set to the neighbour's predicted output flux
 //       (Neumann ghost u_{L-1} = u_{L+1} - 2 dx g, u_{R+1} = u_{R-1} + 2 dx g)
 //       and writes the points of Omega_i not covered by a window further left.
-//   host: next predictive span = ceil((1 + beta) * span) (Sec. 2.6).
-// Simple kernels: one window in shared memory per CTA, a block barrier per
-// step.  The bulk of every span runs on the span kernel.
+//   paper_advance_kernel: the next span starts span levels later, with the
+//       predictive span ceil((1 + beta) * span) (Sec. 2.6).
+// The run's progress lives on the device (PaperState), so the host queues the
+// kernels of many spans and reads the state back once per batch.  Simple
+// kernels: one window in shared memory per CTA, a block barrier per step.
+// The bulk of every span runs on the span kernel.
 
 #include "rswr_internal.h"
 
@@ -107,7 +112,9 @@ __global__ void rswr_iface_kernel(const __grid_constant__ PaperParams<Real> p)
     const int64_t nx = p.nx, N = p.N;
     const int64_t Li = win_l(i, nx, N, p.el), Ri = win_r(i, nx, N, p.er);
     const int64_t Ln = win_l(i + 1, nx, N, p.el), Rn = win_r(i + 1, nx, N, p.er);
-    const int steps = p.steps;
+    if (p.st && p.st->done) return;  // (every thread reads the same word)
+    const int steps = p.st ? p.st->steps : p.steps;
+    const int64_t n0 = p.st ? p.st->n0 : p.n0;
     const int64_t a0 = Ln - steps > Li ? Ln - steps : Li;  // prediction of i: [a0, Ri]
     const int64_t b1 = Ri + steps < Rn ? Ri + steps : Rn;  // prediction of i+1: [Ln, b1]
     const int64_t na = Ri - a0 + 1, nb = b1 - Ln + 1, nov = Ri - Ln + 1;
@@ -132,7 +139,7 @@ __global__ void rswr_iface_kernel(const __grid_constant__ PaperParams<Real> p)
     for (int64_t o = threadIdx.x; o < nov; o += blockDim.x) agree[o] = 0;
     __syncthreads();
     for (int st = 0; st < steps; ++st) {
-        const int64_t n = p.n0 + st;
+        const int64_t n = n0 + st;
         // output flux waveforms at level n: subdomain i at Ln (for i+1), i+1 at Ri (for i)
         if (threadIdx.x == 0) {
             p.gL[(i + 1) * p.tau_stride + st] = rdiv(rsub(ua[Ln + 1 - a0], ua[Ln - 1 - a0]), p.two_dx);
@@ -176,7 +183,9 @@ __global__ void rswr_resolve_kernel(const __grid_constant__ PaperParams<Real> p)
     const int64_t i = p.tile_sub[t], c0 = p.tile_lo[t], c1 = p.tile_hi[t];  // owned [c0, c1) of subdomain i
     const int64_t nx = p.nx, N = p.N;
     const int64_t Li = win_l(i, nx, N, p.el), Ri = win_r(i, nx, N, p.er);
-    const int span = p.steps;
+    const int span = p.st ? p.st->span : p.steps;
+    const int64_t n0 = p.st ? p.st->n0 : p.n0;
+    if (span <= 0) return;  // the run is complete (every thread reads the same word)
     const int64_t lo = c0 - span > Li ? c0 - span : Li;
     const int64_t hi = c1 - 1 + span < Ri ? c1 - 1 + span : Ri;
     const int64_t nw = hi - lo + 1;
@@ -193,7 +202,7 @@ __global__ void rswr_resolve_kernel(const __grid_constant__ PaperParams<Real> p)
     const Real* gL = (i > 0 && Li > 0) ? p.gL + i * p.tau_stride : nullptr;
     const Real* gR = (i + 1 < N && Ri < nx - 1) ? p.gR + i * p.tau_stride : nullptr;
     for (int st = 0; st < span; ++st) {
-        window_step<Real>(p.form, p.c2, p.k, p.two_dx, nx, lo, hi, Li, Ri, gL, gR, st, p.fA, p.fB, p.n0 + st, u, w,
+        window_step<Real>(p.form, p.c2, p.k, p.two_dx, nx, lo, hi, Li, Ri, gL, gR, st, p.fA, p.fB, n0 + st, u, w,
                           u2, w2);
         __syncthreads();
         Real* tt;
@@ -210,8 +219,9 @@ __global__ void rswr_resolve_kernel(const __grid_constant__ PaperParams<Real> p)
 // every zone tile, from the scratch pair (plain arrays) to the state pair.
 template <typename Real>
 __global__ void paper_scatter_kernel(const Real* su, const Real* sw, Real* du, Real* dw, const int64_t* lo,
-                                     const int64_t* hi)
+                                     const int64_t* hi, const PaperState* st)
 {
+    if (st && st->span <= 0) return;  // the run is complete: nothing was re-solved
     const int64_t t = blockIdx.x;
     for (int64_t j = lo[t] + threadIdx.x; j < hi[t]; j += blockDim.x) {
         du[j] = su[j];
@@ -219,19 +229,89 @@ __global__ void paper_scatter_kernel(const Real* su, const Real* sw, Real* du, R
     }
 }
 
+// The select step's end (Sec. 2.4, Sec. 3): the global span is the minimum
+// over the pairs (the word the interface CTAs lowered), at most the
+// predictive steps and the Theorem's cap, at least 1; recorded as span number
+// `count`.  Then the span kernel's boundary samples: levels n0 .. n0+nsamp-1
+// of fA and fB (0 past level T) into fAs, fBs.
+template <typename Real>
+__global__ void paper_select_kernel(PaperState* st, const int* word, int cap, const Real* fA, const Real* fB,
+                                    Real* fAs, Real* fBs, int nsamp, int64_t T, int64_t* spans, int64_t spans_cap)
+{
+    __shared__ int s_span;
+    __shared__ int64_t s_n0;
+    if (threadIdx.x == 0) {
+        int span = 0;
+        if (!st->done) {
+            span = *word < st->steps ? *word : st->steps;
+            if (span > cap) span = cap;
+            if (span < 1) span = 1;
+            if (spans && st->count < spans_cap) spans[st->count] = span;
+        }
+        st->span = span;
+        s_span = span;
+        s_n0 = st->n0;
+    }
+    __syncthreads();
+    if (s_span <= 0) return;
+    for (int i = threadIdx.x; i < nsamp; i += blockDim.x) {
+        const int64_t lv = s_n0 + i;
+        fAs[i] = (fA && lv <= T) ? fA[lv] : Real(0);
+        fBs[i] = (fB && lv <= T) ? fB[lv] : Real(0);
+    }
+}
+
+// The next span (Sec. 2.6): n0 advances by the span, the predictive span
+// becomes ceil((1 + beta) span) (beta in thousandths, exact integer
+// arithmetic) capped at tau_max, the predictive steps min(tau, T - n0).
+__global__ void paper_advance_kernel(PaperState* st, int64_t T, int64_t beta_m, int64_t tau_max)
+{
+    if (st->done || st->span <= 0) return;
+    const int64_t span = st->span;
+    st->n0 += span;
+    st->count += 1;
+    int64_t tau = (span * (1000 + beta_m) + 999) / 1000;
+    if (tau > tau_max) tau = tau_max;
+    st->tau = (int32_t)tau;
+    const int64_t rem = T - st->n0;
+    st->steps = (int32_t)(tau < rem ? tau : rem);
+    st->done = st->n0 >= T ? 1 : 0;
+}
+
 }  // namespace
 
+cudaError_t paper_select_launch(int dtype, PaperState* st, const int* word, int cap, const void* fA, const void* fB,
+                                void* fAs, void* fBs, int nsamp, int64_t T, int64_t* spans, int64_t spans_cap,
+                                cudaStream_t s)
+{
+    if (dtype == kF64)
+        paper_select_kernel<double><<<1, 256, 0, s>>>(st, word, cap, static_cast<const double*>(fA),
+                                                      static_cast<const double*>(fB), static_cast<double*>(fAs),
+                                                      static_cast<double*>(fBs), nsamp, T, spans, spans_cap);
+    else
+        paper_select_kernel<float><<<1, 256, 0, s>>>(st, word, cap, static_cast<const float*>(fA),
+                                                     static_cast<const float*>(fB), static_cast<float*>(fAs),
+                                                     static_cast<float*>(fBs), nsamp, T, spans, spans_cap);
+    return cudaGetLastError();
+}
+
+cudaError_t paper_advance_launch(PaperState* st, int64_t T, int64_t beta_m, int64_t tau_max, cudaStream_t s)
+{
+    paper_advance_kernel<<<1, 1, 0, s>>>(st, T, beta_m, tau_max);
+    return cudaGetLastError();
+}
+
 cudaError_t paper_scatter_launch(int dtype, const void* su, const void* sw, void* du, void* dw, const int64_t* lo,
-                                 const int64_t* hi, int ntiles, cudaStream_t s)
+                                 const int64_t* hi, int ntiles, const PaperState* st, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     if (dtype == kF64)
         paper_scatter_kernel<double><<<ntiles, 128, 0, s>>>(static_cast<const double*>(su),
                                                             static_cast<const double*>(sw), static_cast<double*>(du),
-                                                            static_cast<double*>(dw), lo, hi);
+                                                            static_cast<double*>(dw), lo, hi, st);
     else
         paper_scatter_kernel<float><<<ntiles, 128, 0, s>>>(static_cast<const float*>(su), static_cast<const float*>(sw),
-                                                           static_cast<float*>(du), static_cast<float*>(dw), lo, hi);
+                                                           static_cast<float*>(du), static_cast<float*>(dw), lo, hi, st);
     return cudaGetLastError();
 }
 

@@ -121,7 +121,7 @@ struct Engine {
     // adjoint workspace (rswr_adjoint with dL/da): states, tables, partial sums
     void* adj_mem = nullptr;
     size_t adj_mem_cap = 0;
-    int* h_word = nullptr;  // pinned host word (the paper-literal span read back every span)
+    PaperState* h_pstate = nullptr;  // pinned: the paper-literal run's progress, read back once per batch
     // Span states of a forward run kept in adj_mem for the next rswr_adjoint
     // (rswr_run_keep): valid while `kept` holds and the key matches.
     struct KeptKey {
@@ -178,7 +178,7 @@ void free_engine(Engine* e)
     cudaFree(e->d_ticket);
     cudaFree(e->d_done);
     cudaFree(e->d_xbuf);
-    if (e->h_word) cudaFreeHost(e->h_word);
+    if (e->h_pstate) cudaFreeHost(e->h_pstate);
     cudaFree(e->d_err);
     cudaFree(e->d_host_stage);
     cudaFree(e->adj_mem);
@@ -445,6 +445,7 @@ struct RunReq {
     bool mono = false;
     bool user_src = false;  // apply the engine's user point sources
     bool from_state = false;  // continue from the engine's state q[0] as it is (no level-0 set-up)
+    const int32_t* steps_dev = nullptr;  // the run's length on the device (<= T; SpanParams::steps_dev)
 };
 
 template <typename Real>
@@ -682,6 +683,7 @@ rswr_status device_work(Engine* e, const RunReq& r, int nprobe, int64_t mono_blk
     if (!r.mono) {
         const int nspans = (int)((r.T + e->S - 1) / e->S);
         SpanParams<Real> prm = span_params<Real>(e, r.T, nspans);
+        prm.steps_dev = r.steps_dev;
         int bps = 0;
         RSWR_CUDA(span_occupancy(e->variant, &bps));
         if (bps < 1) return fail(RSWR_ENOTSUP, "span kernel does not fit on an SM");
@@ -1703,7 +1705,15 @@ rswr_status run_paper(Engine* e, const Real* fA, const Real* fB, int64_t T, cons
     const size_t b_state = up(es * nx);
     const size_t b_g = up(es * N * tau_max);
     const size_t b_t = up(sizeof(int64_t) * std::max<int64_t>(nt, 1));
-    const size_t need = 2 * b_state + 2 * b_g + 3 * b_t + 256;
+    // the span kernel runs nsub spans of S steps per paper span (the last ones
+    // may take fewer or none: the span is chosen on the device), reading the
+    // span's boundary samples from a copy of nsamp levels
+    const int64_t nsub = (cap + e->S - 1) / e->S;
+    const int nsamp = (int)(nsub * e->S + 1);
+    const size_t b_samp = up(es * (size_t)nsamp);
+    const int64_t rec_cap = spans ? std::min<int64_t>(spans_cap, std::max<int64_t>(T, 1)) : 0;
+    const size_t b_rec = up(sizeof(int64_t) * (size_t)std::max<int64_t>(rec_cap, 1));
+    const size_t need = 2 * b_state + 2 * b_g + 3 * b_t + 256 + 2 * b_samp + b_rec + up(sizeof(PaperState));
     if (need > e->adj_mem_cap) {
         RSWR_CUDA(cudaStreamSynchronize(s));
         cudaFree(e->adj_mem);
@@ -1721,6 +1731,11 @@ rswr_status run_paper(Engine* e, const Real* fA, const Real* fB, int64_t T, cons
     int64_t* d_lo = reinterpret_cast<int64_t*>(m + 2 * b_state + 2 * b_g + b_t);
     int64_t* d_hi = reinterpret_cast<int64_t*>(m + 2 * b_state + 2 * b_g + 2 * b_t);
     int* d_span = reinterpret_cast<int*>(m + 2 * b_state + 2 * b_g + 3 * b_t);
+    char* m2 = m + 2 * b_state + 2 * b_g + 3 * b_t + 256;
+    Real* d_fAs = reinterpret_cast<Real*>(m2);
+    Real* d_fBs = reinterpret_cast<Real*>(m2 + b_samp);
+    int64_t* d_rec = reinterpret_cast<int64_t*>(m2 + 2 * b_samp);
+    PaperState* d_st = reinterpret_cast<PaperState*>(m2 + 2 * b_samp + b_rec);
     if (nt > 0) {
         RSWR_CUDA(cudaMemcpyAsync(d_sub, tsub.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice, s));
         RSWR_CUDA(cudaMemcpyAsync(d_lo, tlo.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice, s));
@@ -1767,59 +1782,77 @@ rswr_status run_paper(Engine* e, const Real* fA, const Real* fB, int64_t T, cons
     pp.k = sizeof(Real) == 8 ? (Real)ph.k : (Real)ph.kf;
     const double dx = (ph.xb - ph.xa) / (double)(nx - 1);
     pp.two_dx = (Real)(2.0 * dx);
-    if (!e->h_word && cudaMallocHost(&e->h_word, sizeof(int)) != cudaSuccess) {
+    if (!e->h_pstate && cudaMallocHost(&e->h_pstate, sizeof(PaperState)) != cudaSuccess) {
         cudaGetLastError();
-        e->h_word = nullptr;
-        return fail(RSWR_ENOMEM, "pinned host word");
+        e->h_pstate = nullptr;
+        return fail(RSWR_ENOMEM, "pinned host state");
     }
-    int64_t m_count = 0;
-    for (int64_t n0 = 0; n0 < T;) {
-        // the state at level n0, indexed by grid point
-        Real* cu = static_cast<Real*>(e->q0[0]) + ph.base;
-        Real* cw = static_cast<Real*>(e->q1[0]) + ph.base;
-        const int steps = (int)std::min<int64_t>(tau, T - n0);
-        pp.u = cu;
-        pp.w = cw;
-        pp.n0 = n0;
-        pp.steps = steps;
-        // predict + select (Sec. 2.3, 2.4, Sec. 3): every pair lowers the span
-        // word (bytes 0x7f: a value above any span) with atomicMin
-        RSWR_CUDA(cudaMemsetAsync(d_span, 0x7f, sizeof(int), s));
-        const size_t smem_i = es * (8 * (size_t)(ov + steps + 2)) + sizeof(int) * (size_t)(ov + 2);
-        RSWR_CUDA(paper_iface_launch(e->dtype, &pp, (int)(N - 1), smem_i, s));
-        RSWR_CUDA(cudaMemcpyAsync(e->h_word, d_span, sizeof(int), cudaMemcpyDeviceToHost, s));
+    // the run's progress on the device: the span is chosen there, so the host
+    // queues spans without reading each one back
+    {
+        PaperState h0{};
+        h0.n0 = 0;
+        h0.tau = (int32_t)tau;
+        h0.steps = (int32_t)std::min<int64_t>(tau, T);
+        h0.done = T <= 0 ? 1 : 0;
+        *e->h_pstate = h0;
+        RSWR_CUDA(cudaMemcpyAsync(d_st, e->h_pstate, sizeof(PaperState), cudaMemcpyHostToDevice, s));
+    }
+    pp.st = d_st;
+    pp.steps = (int32_t)tau_max;  // (sizes only: the kernels take steps and span from d_st)
+    const size_t smem_i = es * (8 * (size_t)(ov + tau_max + 2)) + sizeof(int) * (size_t)(ov + 2);
+    const size_t smem_r = es * 4 * (size_t)(CH + 2 * cap + 2);
+    int64_t n0 = 0, m_count = 0;
+    while (n0 < T) {
+        // as many spans as the run needs at least (each advances at most cap
+        // levels), so the batch never runs past T; then one read-back
+        const int64_t batch = std::max<int64_t>(1, (T - n0 + cap - 1) / cap);
+        for (int64_t b = 0; b < batch; ++b) {
+            // the state at level n0 (nsub spans of the span kernel per paper
+            // span: after an odd number the state is in buffer 1, swapped below)
+            pp.u = static_cast<Real*>(e->q0[0]) + ph.base;
+            pp.w = static_cast<Real*>(e->q1[0]) + ph.base;
+            // predict + select (Sec. 2.3, 2.4, Sec. 3): every pair lowers the span
+            // word (bytes 0x7f: a value above any span) with atomicMin
+            RSWR_CUDA(cudaMemsetAsync(d_span, 0x7f, sizeof(int), s));
+            RSWR_CUDA(paper_iface_launch(e->dtype, &pp, (int)(N - 1), smem_i, s));
+            RSWR_CUDA(paper_select_launch(e->dtype, d_st, d_span, (int)cap, fA, fB, d_fAs, d_fBs, nsamp, T,
+                                          rec_cap > 0 ? d_rec : nullptr, rec_cap, s));
+            // update (Sec. 2.5): the zones next to input boundaries from the span-start state
+            pp.uo = Y0;
+            pp.wo = Y1;
+            if (nt > 0) RSWR_CUDA(paper_resolve_launch(e->dtype, &pp, (int)nt, smem_r, s));
+            // ... and every other point through the span kernel
+            RunReq r;
+            r.fA = fA ? d_fAs : nullptr;
+            r.fB = fB ? d_fBs : nullptr;
+            r.T = nsub * e->S;
+            r.steps_dev = &d_st->span;
+            r.from_state = true;
+            rswr_status st = run_impl<Real>(e, r, s);
+            if (st != RSWR_OK) return st;
+            if (nsub & 1) {  // the result is in buffer 1: make it the current state
+                std::swap(e->q0[0], e->q0[1]);
+                std::swap(e->q1[0], e->q1[1]);
+            }
+            RSWR_CUDA(paper_scatter_launch(e->dtype, Y0, Y1, static_cast<Real*>(e->q0[0]) + ph.base,
+                                           static_cast<Real*>(e->q1[0]) + ph.base, d_lo, d_hi, (int)nt, d_st, s));
+            RSWR_CUDA(paper_advance_launch(d_st, T, beta_m, tau_max, s));
+        }
+        RSWR_CUDA(cudaMemcpyAsync(e->h_pstate, d_st, sizeof(PaperState), cudaMemcpyDeviceToHost, s));
         RSWR_CUDA(cudaStreamSynchronize(s));
-        int span = std::min(*e->h_word, steps);
-        if (span > cap) span = (int)cap;
-        if (span < 1) span = 1;
-        // update (Sec. 2.5): the zones next to input boundaries from the span-start state
-        pp.steps = span;
-        pp.uo = Y0;
-        pp.wo = Y1;
-        if (nt > 0) {
-            const size_t smem_r = es * 4 * (size_t)(CH + 2 * span + 2);
-            RSWR_CUDA(paper_resolve_launch(e->dtype, &pp, (int)nt, smem_r, s));
+        const int64_t before = n0;
+        n0 = e->h_pstate->n0;
+        m_count = e->h_pstate->count;
+        if (n0 <= before) {
+            rswr_status st = check_engine(e, s, nullptr, nullptr, nullptr);
+            if (st != RSWR_OK) return st;
+            return fail(RSWR_ECUDA, "paper-literal run made no progress");
         }
-        // ... and every other point through the span kernel
-        RunReq r;
-        r.fA = fA ? fA + n0 : nullptr;
-        r.fB = fB ? fB + n0 : nullptr;
-        r.T = span;
-        r.from_state = true;
-        rswr_status st = run_impl<Real>(e, r, s);
-        if (st != RSWR_OK) return st;
-        if (((span + e->S - 1) / e->S) & 1) {  // the result is in buffer 1: make it the current state
-            std::swap(e->q0[0], e->q0[1]);
-            std::swap(e->q1[0], e->q1[1]);
-        }
-        RSWR_CUDA(paper_scatter_launch(e->dtype, Y0, Y1, static_cast<Real*>(e->q0[0]) + ph.base,
-                                       static_cast<Real*>(e->q1[0]) + ph.base, d_lo, d_hi, (int)nt, s));
-        if (spans && m_count < spans_cap) spans[m_count] = span;
-        ++m_count;
-        n0 += span;
-        tau = ((int64_t)span * (1000 + beta_m) + 999) / 1000;
-        if (tau > tau_max) tau = tau_max;
     }
+    if (spans && m_count > 0)
+        RSWR_CUDA(cudaMemcpyAsync(spans, d_rec, sizeof(int64_t) * (size_t)std::min<int64_t>(m_count, rec_cap),
+                                  cudaMemcpyDeviceToHost, s));
     if (nspans) *nspans = m_count;
     RSWR_CUDA(cudaMemcpyAsync(out0, static_cast<Real*>(e->q0[0]) + ph.base, es * nx, cudaMemcpyDeviceToDevice, s));
     RSWR_CUDA(cudaMemcpyAsync(out1, static_cast<Real*>(e->q1[0]) + ph.base, es * nx, cudaMemcpyDeviceToDevice, s));

@@ -88,6 +88,9 @@ struct SpanParams {
                                  // > 0: span k reads q[0] + k * ck_stride and writes
                                  // q[0] + (k + 1) * ck_stride (every span state kept)
     Real* xbuf;                  // resident variants: halo strips, [tile][span parity][side][component][H]
+    const int32_t* steps_dev;    // non-null: the run's length is *steps_dev (<= T), read on the device
+                                 // (the paper-literal path chooses its span there); later spans of the
+                                 // launch then take no steps and pass their tiles through
 };
 
 template <typename Real>
@@ -150,6 +153,18 @@ struct AdjParams {
     int* done;
 };
 
+// The paper-literal run's progress, kept on the device so that the host can
+// queue many spans without reading each span back (paper_kernel.cu).
+struct PaperState {
+    int64_t n0;     // first level of the current span
+    int32_t tau;    // predictive span (Sec. 2.6)
+    int32_t steps;  // predictive steps of the current span: min(tau, T - n0)
+    int32_t span;   // the span selected for the current span (0: the run is complete)
+    int32_t count;  // spans taken so far
+    int32_t done;   // 1 once n0 has reached T
+    int32_t pad_;
+};
+
 // The paper-literal span (paper_kernel.cu): plain (unpadded) state arrays.
 template <typename Real>
 struct PaperParams {
@@ -169,6 +184,7 @@ struct PaperParams {
     int32_t steps;   // predictive steps (iface kernel) or selected span (re-solve kernel)
     int32_t form;
     Real c2, k, two_dx;
+    const PaperState* st;  // non-null: n0, steps and the span come from here (n0 / steps above unused)
 };
 
 struct VariantInfo {
@@ -217,8 +233,12 @@ cudaError_t adj_reduce_launch(const double* partial, int64_t nspans, int64_t nti
 
 // paper_kernel.cu
 cudaError_t paper_scatter_launch(int dtype, const void* su, const void* sw, void* du, void* dw, const int64_t* lo,
-                                 const int64_t* hi, int ntiles, cudaStream_t s);
+                                 const int64_t* hi, int ntiles, const PaperState* st, cudaStream_t s);
 cudaError_t paper_iface_launch(int dtype, const void* params, int n_iface, size_t smem, cudaStream_t s);
+cudaError_t paper_select_launch(int dtype, PaperState* st, const int* word, int cap, const void* fA, const void* fB,
+                                void* fAs, void* fBs, int nsamp, int64_t T, int64_t* spans, int64_t spans_cap,
+                                cudaStream_t s);
+cudaError_t paper_advance_launch(PaperState* st, int64_t T, int64_t beta_m, int64_t tau_max, cudaStream_t s);
 cudaError_t paper_resolve_launch(int dtype, const void* params, int ntiles, size_t smem, cudaStream_t s);
 
 // rswr_api.cu: sets the message returned by rswr_last_error_message()

@@ -95,6 +95,17 @@ __device__ bool wait_deps(const SpanParams<Real>& prm, long long t)
     }
 }
 
+// Steps of the launch's span that starts at level n0: S, or what is left of
+// the run.  The run's length is T, or *steps_dev when the span is chosen on
+// the device (then a span past it takes no steps: its tiles pass through).
+template <typename Real>
+__device__ __forceinline__ int span_steps(const SpanParams<Real>& prm, int64_t n0)
+{
+    const int64_t T = prm.steps_dev ? (int64_t)*prm.steps_dev : prm.T;
+    const int64_t r = T - n0;
+    return (int)(r < 0 ? 0 : (r < prm.S ? r : prm.S));
+}
+
 // State arrays read (span k) and written (span k + 1) by a span; comp 0 / 1
 // selects the first / second component.
 template <typename Real>
@@ -548,7 +559,7 @@ __global__ void __launch_bounds__(NT, MINB) span_kernel(const __grid_constant__ 
         const ProblemDev<Real>& pr = prm.problems[td.problem];
         const int64_t gj0 = (int64_t)td.local * prm.core - prm.H;  // problem coordinate of window start
         const int64_t n0 = (int64_t)k * prm.S;
-        const int steps = (int)((prm.T - n0 < prm.S) ? (prm.T - n0) : prm.S);
+        const int steps = span_steps(prm, n0);
         const bool edge = (gj0 <= 0) || (gj0 + W - 1 >= pr.nx - 1);
         const int tb = warp * G::CW + lane * P;  // window index of the thread's first point
         int own_lo, own_hi;
@@ -730,7 +741,7 @@ __device__ void producer_loop(const SpanParams<Real>& prm, Real* stage, uint64_t
             si.k = k;
             si.tile = tile;
             si.np = np;
-            si.steps = (int)((prm.T - n0 < prm.S) ? (prm.T - n0) : prm.S);
+            si.steps = span_steps(prm, n0);
             si.edge = (gj0 <= 0) || (gj0 + W - 1 >= pr.nx - 1);
             if (np > 0 && np <= kTileProbes)
                 for (int q = 0; q < np; ++q) sprobes[y][q] = prm.probes[td.probe_begin + q];
@@ -988,7 +999,7 @@ __global__ void __launch_bounds__(NT, MINB) span_kernel_res(const __grid_constan
 
     for (int k = 0; k < prm.nspans; ++k) {
         const int64_t n0 = (int64_t)k * prm.S;
-        const int steps = (int)((prm.T - n0 < prm.S) ? (prm.T - n0) : prm.S);
+        const int steps = span_steps(prm, n0);
         Real u[P], w[P];
         smem_to_regs<Real, P>(su + tb, u);
         smem_to_regs<Real, P>(sw + tb, w);
