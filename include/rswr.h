@@ -301,12 +301,15 @@ rswr_status rswr_run_keep(rswr_plan_t plan, const void* fA, const void* fB, int6
  *   grad_a[0]  = dL/da       (one double, device pointer; NULL skips it).
  * The adjoint variables obey the leapfrog backward in time with zero
  * Dirichlet data and the source wbar at j_r; they run through the same span
- * kernel.  dL/da pairs them with the forward levels, recomputed inside
- * shared memory from span-boundary states: by default every span state is kept
- * when they fit in half of the free device memory (one forward sweep, then one
- * persistent adjoint launch over all spans), else one checkpoint every
- * ceil(sqrt(#spans)) spans with the states of each segment recomputed before
- * its spans are processed (rswr_plan_set_checkpoint_spacing overrides).
+ * kernel.  dL/da pairs them with the forward levels, recomputed on chip
+ * from span-boundary states (the levels' Laplacians kept in shared memory,
+ * or in tensor memory by the persistent FP32 sweep): by default every span
+ * state is kept when they fit in half of the free device memory (one forward
+ * sweep -- one resident launch when the plan's variant is a resident one and
+ * its tiles fit -- then one persistent adjoint launch over all spans), else
+ * one checkpoint every ceil(sqrt(#spans)) spans with the states of each
+ * segment recomputed before its spans are processed
+ * (rswr_plan_set_checkpoint_spacing overrides).
  * Canonical plans give grad_fA bit-identical to a plain FP64 discrete adjoint
  * of the canonical leapfrog.
  */
