@@ -834,6 +834,46 @@ def test_paper_literal_equals_oracle_bitwise(R, oracle_mod, form, nx, N, ov, cfl
     assert np.abs(host(got["u"]) - mono["u"]).max() <= 1e-12 * np.abs(mono["u"]).max()
 
 
+# tiny grids on which the paper's select binds below the Theorem's cap (the
+# oracle's span rule is pinned on the same geometries): nx, N, ov, Courant
+# number, T; a dyadic boundary pulse
+PAPER_BINDING_CASES = [(33, 2, 8, 0.5, 60), (40, 3, 8, 0.3, 70), (41, 3, 10, 0.6, 80), (29, 2, 6, 0.9, 50)]
+
+
+@pytest.mark.parametrize("form", [CAN, INC])
+@pytest.mark.parametrize("nx,N,ov,cfl,T", PAPER_BINDING_CASES)
+def test_paper_literal_binding_select_bitwise(R, oracle_mod, form, nx, N, ov, cfl, T):
+    """Spans chosen below the cap by the data: the device-side span choice
+    needs several batches of queued spans (a batch is the fewest spans that
+    could finish the run), and the span sequence and the state still equal
+    the oracle's bit for bit."""
+    dt = cfl / (nx - 1)
+    m = np.arange(T + 1)
+    fA = np.where((m > 0) & (m < 8), np.round(np.sin(np.pi * m / 8) ** 2 * 64) / 64, 0.0)
+    z = np.zeros(T + 1)
+    plan = R.Plan(0.0, 1.0, 1.0, nx, dt, N, ov, dtype=F64, form=form)
+    got = plan.run_paper(fA, None, T)
+    ref = oracle_mod.rswr_paper(nx, T, 1.0, dt, fA, z, N, ov, form=ORACLE_FORM[form])
+    assert list(got["spans"]) == list(ref["spans"])
+    assert sum(got["spans"]) == T
+    assert_bitwise(host(got["u"]), ref["u"], "paper-literal u")
+    assert_bitwise(host(got["w"]), ref["w"], "paper-literal w")
+
+
+def test_paper_literal_binding_select_reached_below_the_cap(oracle_mod):
+    """(CPU) the cases above do take spans below the Theorem's cap, so the
+    device loop needs more than one batch on them."""
+    below = 0
+    for nx, N, ov, cfl, T in PAPER_BINDING_CASES:
+        dt = cfl / (nx - 1)
+        m = np.arange(T + 1)
+        fA = np.where((m > 0) & (m < 8), np.round(np.sin(np.pi * m / 8) ** 2 * 64) / 64, 0.0)
+        spans = oracle_mod.rswr_paper(nx, T, 1.0, dt, fA, np.zeros(T + 1), N, ov)["spans"]
+        cap = int(np.ceil((ov - 1) / (2 * cfl))) - 1
+        below += int(min(spans[:-1]) < cap) if len(spans) > 1 else 0
+    assert below >= 3
+
+
 def test_paper_literal_fp32_close_to_fp64(R, oracle_mod):
     nx, N, ov, T = 20001, 16, 32, 3000
     dt = 0.9 / (nx - 1)
