@@ -581,6 +581,23 @@ def profile_case(which: str, variant=None, span=None, full=False, log2_nx=22) ->
         plan.check()
         print(json.dumps({"profile_case": which, "nx": p.nx, "T": p.T, "info": plan.info()}))
         return
+    if which in ("paper64", "paper32"):
+        # the paper-literal run on the c2 grid, 2000 steps (once to warm, once to capture)
+        p = inputs.c2(T=2000)
+        dtype = rswr.F64 if which == "paper64" else rswr.F32
+        td = torch.float64 if dtype == rswr.F64 else torch.float32
+        plan = rswr.Plan.from_problem(p, dtype=dtype)
+        if span is not None:
+            plan.set_span(span)
+        if variant is not None:
+            plan.set_variant(variant)
+        fA = torch.as_tensor(p.fA, device="cuda").to(td)
+        for _ in range(2):
+            r = plan.run_paper(fA, None, p.T)
+        torch.cuda.synchronize()
+        plan.check()
+        print(json.dumps({"profile_case": which, "nx": p.nx, "T": p.T, "spans": len(r["spans"]), "info": plan.info()}))
+        return
     if which in ("adj64", "adj32"):
         # the c4 gradient workload (dL/dfA and dL/da), run twice; a smaller grid
         # (log2_nx < 20) scales the steps with it
@@ -1005,9 +1022,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mono", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched / adjoint / large-grid measurements")
-    ap.add_argument("--profile-case", choices=["f64", "f32", "adj64", "adj32", "g32", "c3"], default=None,
+    ap.add_argument("--profile-case", choices=["f64", "f32", "adj64", "adj32", "g32", "c3", "paper64", "paper32"],
+                    default=None,
                     help="run a small profiling case twice and exit (for ncu): f64/f32 nx=2^22, 1280 steps; "
-                         "adj64/adj32 the c4 gradient; c3 the first 1024 batched problems, 256 steps")
+                         "adj64/adj32 the c4 gradient; c3 the first 1024 batched problems, 256 steps; "
+                         "paper64/paper32 the paper-literal run on the c2 grid, 2000 steps")
     ap.add_argument("--variant", type=int, default=None, help="kernel variant of the profiling case")
     ap.add_argument("--profile-log2-nx", type=int, default=None,
                     help="grid of the profiling case: 2^N points (default 22; 24 = the bench grid; "
